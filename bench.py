@@ -1,0 +1,398 @@
+"""Benchmark of the Nekbone hot path on one GB300 (or N replicas).
+
+A step is one fixed-iteration CG solve (500 iterations, tol <= 0) of the
+synthetic Nekbone box problem with E = 4096 elements (16 x 16 x 16) and
+n = 10 GLL points per direction (degree 9), FP64: every iteration runs ax_e
+fused with p = r + beta p, dssum, mask, <w,p>_c and the x/r update with
+<r,r>_c.  The metric is Ax throughput in GDOF/s: local points (E n^3) times
+CG iterations, divided by the device time.  The working set (gxyz 197 MB +
+five 33 MB vectors) is larger than the 129 MB L2, so no flush is needed
+between iterations; the standalone ax_e timings below flush L2.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+N > 1 runs under torchrun as independent replicas (weak scaling): each rank
+solves its own copy of the problem; the only collectives are the timing
+barrier and the max-over-ranks of the elapsed time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2005_13425_gb300 import inputs, metrics  # noqa: E402
+
+METRIC = "Ax GDOF/s, % HBM roofline (N=10); served solves/s + p99, mixed vs FP64"
+DIMS = (16, 16, 16)
+NGLL = 10
+CG_ITERS = 500
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Dist:
+    """Barrier and max-over-ranks of host scalars (replicas only)."""
+
+    def __init__(self, world: int, backend: str):
+        self.world = world
+        self.pg = None
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend=backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max(self, value: float) -> float:
+        if self.world == 1:
+            return value
+        import torch
+        dev = "cuda" if self.dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([value], dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.world > 1:
+            self.dist.destroy_process_group()
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.th.join(timeout=5)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def hardware_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ---------------------------------------------------------------- oracle arm
+def oracle_problem():
+    import oracle
+    s = inputs.perturbation_coeffs(inputs.SEED_MESH)
+    P = oracle.box_problem(*DIMS, NGLL, inputs.PERTURB_AMP, s)
+    fu = inputs.unique_field(*DIMS, NGLL, inputs.SEED_F)
+    f = oracle.apply_mask(P["mask"], oracle.scatter_unique(*DIMS, NGLL, fu))
+    return oracle, P, f
+
+
+def time_oracle_cg(iters: int):
+    """Wall time of the oracle's CG for `iters` fixed iterations."""
+    oracle, P, f = oracle_problem()
+    t0 = time.perf_counter()
+    _, it, _, _, _ = oracle.cg(*DIMS, NGLL, P["D"], P["gxyz"], P["mask"], f, tol=0.0, maxit=iters)
+    dt = time.perf_counter() - t0
+    return dt, it
+
+
+def cpu_baseline(iters: int = 4):
+    dt, it = time_oracle_cg(iters)
+    dofs = P_dofs()
+    return {"value": dofs * it / dt / 1e9, "unit": "GDOF/s", "cores": hardware_threads(),
+            "kind": "oracle", "cpu": cpu_model(),
+            "sample": f"{it} fixed CG iterations (plus the initial residual) of the same "
+                      f"E=4096, n=10 problem, wall {dt:.2f} s"}
+
+
+def P_dofs() -> int:
+    return DIMS[0] * DIMS[1] * DIMS[2] * NGLL ** 3
+
+
+def run_reference(args, rank, world):
+    """The oracle, as it stands, on the host cores: the reference arm."""
+    if rank != 0:
+        return 0
+    per_step = 2
+    for _ in range(args.warmup):
+        time_oracle_cg(per_step)
+    times = []
+    for _ in range(args.steps):
+        dt, it = time_oracle_cg(per_step)
+        times.append(dt)
+    total = sum(times)
+    value = P_dofs() * per_step * args.steps / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GDOF/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "nekbone_box_16x16x16_n10_cg_fp64", "E": 4096, "n": NGLL,
+                   "cg_iterations_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": hardware_threads(),
+                         "kind": "oracle", "cpu": cpu_model(),
+                         "sample": f"{per_step} CG iterations (+ initial residual) per step, "
+                                   f"E=4096, n=10, oracle CG with OpenMP ax_e"},
+        "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world, local):
+    import torch
+
+    from paper_2005_13425_gb300 import nekgb
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = Dist(world, "nccl")
+    nekgb.load()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    E = DIMS[0] * DIMS[1] * DIMS[2]
+    D = E * NGLL ** 3
+    s = inputs.perturbation_coeffs(inputs.SEED_MESH)
+    ctx = nekgb.nb_setup_box(DIMS, NGLL, inputs.PERTURB_AMP, s, nekgb.NB_FP64, stream)
+    info = nekgb.nb_get_info(ctx)
+    fu = torch.from_numpy(inputs.unique_field(*DIMS, NGLL, inputs.SEED_F)).cuda()
+    f = torch.empty(E, NGLL ** 3, dtype=torch.float64, device="cuda")
+    nekgb.nb_scatter_unique(ctx, fu, f)
+    nekgb.nb_mask(ctx, f)
+    x = torch.zeros_like(f)
+
+    def step():
+        x.zero_()
+        nekgb.nb_cg_solve(ctx, f, x, tol=0.0, maxit=CG_ITERS)
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+
+    # ---- timed region: per-kernel events on the library's stream
+    nekgb.nb_timing_enable(ctx, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    dist.barrier()
+    t_ms = dist.max(ev0.elapsed_time(ev1))
+    kern = {}
+    launches = 0
+    for kid, name in nekgb.KERNEL_NAMES.items():
+        ms, cnt = nekgb.nb_timing_read(ctx, kid)
+        kern[name] = {"ms_total": ms, "launches": cnt}
+        launches += cnt
+    nekgb.nb_timing_enable(ctx, False)
+    value = world * D * CG_ITERS * args.steps / (t_ms * 1e-3) / 1e9
+
+    # ---- the same steps with CUDA graphs (timing off), for reference
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_graph = dist.max(e0.elapsed_time(e1))
+    value_graph = world * D * CG_ITERS * args.steps / (t_graph * 1e-3) / 1e9
+
+    # ---- e2e: host buffers through the C ABI, copies inside the timed region
+    f_host = torch.empty(E * NGLL ** 3, dtype=torch.float64).pin_memory()
+    f_host.copy_(f.reshape(-1).cpu())
+    x_host = torch.zeros(E * NGLL ** 3, dtype=torch.float64).pin_memory()
+    xh = x_host.numpy()
+    fh = f_host.numpy()
+    for _ in range(1):
+        xh[:] = 0.0
+        nekgb.nb_cg_solve_host(ctx, fh, xh, tol=0.0, maxit=CG_ITERS)
+    dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xh[:] = 0.0
+        nekgb.nb_cg_solve_host(ctx, fh, xh, tol=0.0, maxit=CG_ITERS)
+    t_e2e = dist.max(time.perf_counter() - t0)
+    value_e2e = world * D * CG_ITERS * args.steps / t_e2e / 1e9
+
+    # ---- ax_e alone and ax_e + dssum, L2 flushed between repetitions
+    u = torch.from_numpy(inputs.local_field(E, NGLL, inputs.SEED_U)).cuda()
+    w = torch.empty_like(u)
+    l2 = torch.cuda.get_device_properties(local).L2_cache_size
+    scrub = torch.empty(2 * l2 // 4 + 1024, dtype=torch.float32, device="cuda")
+
+    def timed(fn, reps=20):
+        out = []
+        for _ in range(reps):
+            scrub.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+        return statistics.median(out)
+
+    nekgb.nb_ax(ctx, u, w)
+    t_ax = timed(lambda: nekgb.nb_ax(ctx, u, w))
+    t_axds = timed(lambda: (nekgb.nb_ax(ctx, u, w), nekgb.nb_dssum(ctx, w)))
+
+    # ---- roofline of the dominant kernel, from the timed region's events
+    hbm, _, peak_src = metrics.measured_peaks(ROOT)
+    ax = kern["ax_e"]
+    ax_avg_ms = ax["ms_total"] / max(ax["launches"], 1)
+    ax_bytes = metrics.ax_bytes_per_point(8) * D
+    ax_flops = metrics.ax_flops_per_point(NGLL) * D
+    ach_gbs = ax_bytes / (ax_avg_ms * 1e-3) / 1e9
+    ach_tf = ax_flops / (ax_avg_ms * 1e-3) / 1e12
+    hbm_frac = ach_gbs / hbm
+    alu_frac = ach_tf / metrics.NOMINAL_FP64_TFLOPS
+    total_kernel_ms = sum(v["ms_total"] for v in kern.values())
+    variant = nekgb.nb_get_info(ctx)["ax_variant"]
+    roof_hbm = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": hbm_frac, "traffic": None,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "kernel": "ax_e", "algorithmic_bytes_per_launch": ax_bytes,
+                "avg_launch_ms": ax_avg_ms, "launches": ax["launches"]}
+    roof_alu = {"bound": "alu", "achieved": ach_tf, "peak": metrics.NOMINAL_FP64_TFLOPS,
+                "unit": "TFLOP/s", "frac": alu_frac, "traffic": None,
+                "peak_source": "recipe nominal GB300 FP64 1.25 TFLOP/s",
+                "kernel": "ax_e", "algorithmic_flops_per_launch": ax_flops,
+                "avg_launch_ms": ax_avg_ms, "launches": ax["launches"]}
+    roofline = roof_hbm if hbm_frac >= alu_frac else roof_alu
+    other_roofline = roof_alu if roofline is roof_hbm else roof_hbm
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "nekbone_box_16x16x16_n10_cg500_fp64", "E": E, "n": NGLL,
+                   "mesh": "16x16x16", "cg_iterations_per_step": CG_ITERS, "local_dofs": D,
+                   "unique_dofs": int(info["nunique"]), "perturbation": inputs.PERTURB_AMP,
+                   "l2": "inputs larger than L2 (gxyz 197 MB + 5 vectors of 33 MB > 129 MB)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "ax_variant": variant},
+        "roofline": roofline,
+        "roofline_other": other_roofline,
+        "gpu_launches": launches,
+        "kernels_timed_region": kern,
+        "kernel_share": {k: v["ms_total"] / total_kernel_ms for k, v in kern.items() if total_kernel_ms},
+        "value_graph_mode": value_graph,
+        "eq1_gflops": value * metrics.cg_flops_per_point(NGLL),
+        "paper_units_gbs": value * metrics.cg_bytes_per_point(),
+        "ax_only": {"ms": t_ax, "gdofs": D / (t_ax * 1e-3) / 1e9,
+                    "hbm_frac": metrics.ax_bytes_per_point(8) * D / (t_ax * 1e-3) / 1e9 / hbm,
+                    "l2": "flushed between reps"},
+        "ax_dssum": {"ms": t_axds, "gdofs": D / (t_axds * 1e-3) / 1e9},
+        "e2e": {"value": value_e2e, "unit": "GDOF/s",
+                "h2d_bytes_per_step": 2 * 8 * D, "d2h_bytes_per_step": 8 * D,
+                "api": "nb_cg_solve_host (pinned host f, x)"},
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    nekgb.nb_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line))
+    dist.close()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gpu(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,229 @@
+/*
+ * nekgb.h -- C ABI of the GB300-native Nekbone hot path.
+ *
+ * The library evaluates the spectral-element Poisson operator of Nekbone
+ * (Karp et al., "Optimization of Tensor-product Operations in Nekbone on
+ * GPUs", arXiv 2005.13425) on one NVIDIA GB300 (sm_103a):
+ *
+ *   Ax = mask( dssum( ax_e(u) ) )
+ *
+ * where ax_e is the element-local tensor-product operator of Listing 1
+ * (Sec. III), dssum is the direct-stiffness summation that "communicates
+ * the local results to the neighbouring elements" (Sec. III, second step of
+ * Ax), and the mask applies homogeneous Dirichlet conditions (Sec. VI.B).
+ * nb_cg_solve runs the unpreconditioned conjugate-gradient solve of
+ * Ax = f (Sec. III; no preconditioner, Sec. VII) with all vector updates
+ * and reductions on the device.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Mesh: a structured box of Ex x Ey x Ez hexahedral elements covering the
+ *   unit cube, element id e = ex + Ex*(ey + Ey*ez).
+ * n: GLL points per direction (n = polynomial degree + 1), 2 <= n <= 16.
+ * Local storage ("[E][n^3]"): a field holds one double per local point,
+ *   u[e*n^3 + i + n*(j + n*k)], i fastest, exactly Listing 1's u(i,j,k,e).
+ *   Points shared by several elements are stored once per element.
+ * Global node of (e; i,j,k): (gx,gy,gz) = (ex(n-1)+i, ey(n-1)+j, ez(n-1)+k),
+ *   gid = gx + NX*(gy + NY*gz), NX = Ex(n-1)+1, NY = Ey(n-1)+1,
+ *   NZ = Ez(n-1)+1.
+ * D: row major, D[i*n + l] = dxm1(i,l) = derivative of the l-th Lagrange
+ *   basis polynomial at GLL node i (Listing 1's dxm1; dxtm1 = D^T).
+ * gxyz: [E][6][n^3], components rr, rs, rt, ss, st, tt, i.e. Listing 1's
+ *   gxyz(i,j,k,1..6,e) = w_i w_j w_k |J| (J^-1 J^-T).
+ * Device pointers ("_dev") are CUDA device addresses of doubles (8-byte
+ *   aligned, contiguous, local storage), owned by the caller; the library
+ *   never frees them.  Host pointers ("_host") are plain host memory.
+ * Streams: every call is enqueued on the stream given to nb_setup* and is
+ *   asynchronous unless stated otherwise.  Inputs and outputs may not alias
+ *   unless stated.
+ * Errors: every entry point returns an nb_status; nothing is thrown or
+ *   aborted across the ABI.  Argument checks happen before any work.  A
+ *   thread-local message for the last failure is available from
+ *   nb_last_error().  CUDA failures map to NB_ERR_CUDA, failed
+ *   allocations to NB_ERR_OOM.
+ */
+#ifndef NEKGB_H
+#define NEKGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nb_ctx nb_ctx; /* opaque; owns all device-side mesh state */
+
+typedef enum {
+    NB_OK = 0,
+    NB_ERR_ARG = 1,           /* bad argument: size, pointer, alignment */
+    NB_ERR_CUDA = 2,          /* a CUDA runtime call or launch failed */
+    NB_ERR_OOM = 3,           /* device or pinned-host allocation failed */
+    NB_ERR_NOT_CONVERGED = 4, /* tol > 0 and maxit reached first */
+    NB_ERR_BREAKDOWN = 5,     /* CG breakdown: <Ap,p>_c <= 0 or not finite */
+    NB_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+    NB_ERR_STATE = 7          /* call not valid in the context's state */
+} nb_status;
+
+typedef enum {
+    NB_FP64 = 0,  /* FP64-accurate everywhere */
+    NB_MIXED = 1  /* FP32 inner operator inside FP64 defect correction */
+} nb_precision;
+
+typedef struct {
+    int ex, ey, ez; /* elements per direction; E = ex*ey*ez */
+} nb_box;
+
+typedef struct {
+    int ex, ey, ez, n;
+    int64_t nelt;      /* E */
+    int64_t npts;      /* E * n^3 local points */
+    int64_t nunique;   /* NX * NY * NZ unique nodes */
+    int precision;     /* nb_precision */
+    int ax_variant;    /* kernel used by nb_ax (see nb_set_ax_variant) */
+    size_t device_bytes; /* device memory owned by the context */
+} nb_info;
+
+/* --------------------------------------------------------------------- */
+/* Set-up and tear-down                                                  */
+/* --------------------------------------------------------------------- */
+
+/* Build a context for the box `mesh` with n GLL points per direction from
+ * caller-supplied operator data (the inputs of Listing 1).
+ *   D     host, n*n doubles, D[i*n+l] = dxm1(i,l).
+ *   gxyz  host, E*6*n^3 doubles, [E][6][n^3] (rr,rs,rt,ss,st,tt).
+ *   mask  host, E*n^3 bytes, 1 = keep, 0 = Dirichlet (set to +0.0); NULL
+ *         selects homogeneous Dirichlet on all six faces of the box.
+ *   prec  NB_FP64 or NB_MIXED.
+ *   cuda_stream  cudaStream_t to enqueue all work on (NULL = default).
+ * The context copies D, gxyz and mask to the device; the caller keeps
+ * ownership of its arrays.  On failure *out is NULL and nothing leaks. */
+nb_status nb_setup(nb_ctx **out, nb_box mesh, int n, const double *D,
+                   const double *gxyz, const uint8_t *mask, nb_precision prec,
+                   void *cuda_stream);
+
+/* Build the synthetic Nekbone box problem on the device: GLL nodes and
+ * weights, D, and gxyz for the unit cube perturbed by
+ *   x_d = X_d + amp * s[d] * sin(pi X) sin(pi Y) sin(pi Z),  d = 0,1,2
+ * (the perturbation vanishes on the boundary, so the box mask applies).
+ * s: host, 3 doubles.  Fails with NB_ERR_ARG if the map folds (|J| <= 0). */
+nb_status nb_setup_box(nb_ctx **out, nb_box mesh, int n, double amp,
+                       const double *s, nb_precision prec, void *cuda_stream);
+
+/* Free every device resource of the context (synchronises its stream).
+ * NULL is accepted. */
+nb_status nb_destroy(nb_ctx *ctx);
+
+nb_status nb_get_info(const nb_ctx *ctx, nb_info *info);
+
+/* --------------------------------------------------------------------- */
+/* Operator pieces (Sec. III: Ax computed in two steps)                   */
+/* --------------------------------------------------------------------- */
+
+/* w = ax_e(u) element by element (Listing 1), no dssum, no mask.
+ * u_dev, w_dev: device, E*n^3 doubles, must not overlap. */
+nb_status nb_ax(nb_ctx *ctx, const double *u_dev, double *w_dev);
+
+/* In place: each global node's value becomes the sum of its local copies,
+ * added from +0.0 in ascending element order, written back to every copy
+ * (direct stiffness summation, Sec. III).  Bit-for-bit deterministic. */
+nb_status nb_dssum(nb_ctx *ctx, double *w_dev);
+
+/* In place: w := +0.0 at Dirichlet points (a select, not a product). */
+nb_status nb_mask(nb_ctx *ctx, double *w_dev);
+
+/* w = mask(dssum(ax_e(u))): the assembled operator. */
+nb_status nb_apply(nb_ctx *ctx, const double *u_dev, double *w_dev);
+
+/* --------------------------------------------------------------------- */
+/* Conjugate gradient (Sec. III; 100 fixed iterations in Sec. V)          */
+/* --------------------------------------------------------------------- */
+
+/* Solve A x = f by unpreconditioned CG with the weighted inner product
+ * <a,b>_c = sum_local a*b/multiplicity (the unique-node dot product):
+ *   r = f - A x0, p = 0, rho = <r,r>_c
+ *   repeat: stop if rho == 0 or (tol > 0 and sqrt(rho/<f,f>_c) <= tol)
+ *           beta = rho/rho_old (0 first), p = r + beta p, w = A p,
+ *           alpha = rho/<w,p>_c, x += alpha p, r -= alpha w
+ * f_dev: device, E*n^3, continuous and masked.  x_dev: device, in: initial
+ * guess, out: solution.  tol <= 0 runs exactly maxit iterations (the
+ * paper's fixed-iteration mode).  iters_out/relres_out (host, optional)
+ * receive the iterations done and sqrt(<r,r>_c/<f,f>_c).  Blocks until the
+ * solve is finished.  Returns NB_ERR_NOT_CONVERGED if tol > 0 was not
+ * reached within maxit, NB_ERR_BREAKDOWN if <w,p>_c <= 0 or not finite
+ * (x then holds the last good iterate).  For NB_MIXED contexts this runs
+ * FP32-operator CG inside FP64 defect correction (see nb_mixed_solve). */
+nb_status nb_cg_solve(nb_ctx *ctx, const double *f_dev, double *x_dev,
+                      double tol, int maxit, int *iters_out, double *relres_out);
+
+/* The same solve from host buffers: f_host is copied to the device, x_host
+ * (initial guess in, solution out) is copied both ways.  Plain or pinned
+ * host memory; E*n^3 doubles each. */
+nb_status nb_cg_solve_host(nb_ctx *ctx, const double *f_host, double *x_host,
+                           double tol, int maxit, int *iters_out,
+                           double *relres_out);
+
+/* rho_k = <r_k,r_k>_c of the last FP64 solve, k = 0..iters (host copy).
+ * Writes min(cap, iters+1) values, *count = iters + 1. */
+nb_status nb_cg_history(nb_ctx *ctx, double *rho_host, int cap, int *count);
+
+/* --------------------------------------------------------------------- */
+/* Helpers used by the solver, exposed for tests and applications        */
+/* --------------------------------------------------------------------- */
+
+/* *out_host = <a,b>_c (deterministic; blocks until done). */
+nb_status nb_dot_c(nb_ctx *ctx, const double *a_dev, const double *b_dev,
+                   double *out_host);
+
+/* local_dev[e][p] = g_dev[gid(e,p)]: copy a field given per unique node
+ * (NX*NY*NZ doubles, x fastest) to every local copy. */
+nb_status nb_scatter_unique(nb_ctx *ctx, const double *g_dev, double *local_dev);
+
+/* Index work of dssum and mask, for bit-exact checks: any pointer may be
+ * NULL.  gid_dev: int64 [E][n^3]; mult_dev: int32 [E][n^3] (copies of the
+ * point's node); mask_dev: uint8 [E][n^3] (the mask in force). */
+nb_status nb_tables(nb_ctx *ctx, int64_t *gid_dev, int32_t *mult_dev,
+                    uint8_t *mask_dev);
+
+/* Copy out the operator data the context holds: D_host (n*n) and/or
+ * gxyz_dev (device, [E][6][n^3]).  Either may be NULL. */
+nb_status nb_get_operator(nb_ctx *ctx, double *D_host, double *gxyz_dev);
+
+/* Select the ax_e kernel: 0 = automatic (fastest FP64-accurate kernel),
+ * 1 = native FP64 layer kernel, 2 = double-float (FP32-pair) kernel.  All
+ * variants meet the same accuracy contract. */
+nb_status nb_set_ax_variant(nb_ctx *ctx, int variant);
+
+/* --------------------------------------------------------------------- */
+/* Kernel timing (CUDA events recorded on the context's stream)           */
+/* --------------------------------------------------------------------- */
+
+typedef enum {
+    NB_K_AX = 0,      /* ax_e (alone or fused with the CG p update) */
+    NB_K_DSSUM = 1,   /* dssum (+ mask in the solver) */
+    NB_K_MASK = 2,
+    NB_K_DOT = 3,     /* weighted dot products and their finalisation */
+    NB_K_UPDATE = 4,  /* CG x/r updates + <r,r>_c */
+    NB_K_OTHER = 5,
+    NB_K_COUNT = 6
+} nb_kernel_id;
+
+/* on != 0: record an event pair around every kernel launch (CUDA graphs
+ * are not used while timing is on); off: release the records. */
+nb_status nb_timing_enable(nb_ctx *ctx, int on);
+
+/* Accumulated device time (ms) and launch count per kernel class since
+ * timing was enabled or last reset (synchronises the stream). */
+nb_status nb_timing_read(nb_ctx *ctx, int kernel_id, double *ms_total,
+                         int64_t *launches, int reset);
+
+/* --------------------------------------------------------------------- */
+/* Status                                                                */
+/* --------------------------------------------------------------------- */
+const char *nb_status_str(nb_status s);
+const char *nb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NEKGB_H */

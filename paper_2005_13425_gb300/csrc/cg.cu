@@ -1,0 +1,381 @@
+// Unpreconditioned conjugate gradient for Ax = f on the device (arXiv
+// 2005.13425 Sec. III: Nekbone solves the SEM Poisson system with CG;
+// Sec. V: 100 fixed iterations; Sec. VII: no preconditioner), plus the
+// deterministic weighted inner product <a,b>_c = sum a*b/multiplicity.
+//
+// Every scalar of the iteration (rho, alpha, beta, <w,p>_c) lives on the
+// device.  Reductions are two-level and deterministic: each CTA reduces a
+// fixed slice of the points with a fixed shuffle tree, writes one partial,
+// and the last CTA to finish (ticket counter) sums the partials in a fixed
+// order and performs the scalar step.  One iteration is four kernels
+// (ax_e fused with p = r + beta p; dssum; mask; <w,p>_c + alpha;
+// x/r update + <r,r>_c + beta), captured in chunks as a CUDA graph.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace nekgb {
+
+nb_status launch_ax_fp64(nb_ctx *c, const double *u, double *w, int mode);
+nb_status launch_ax_df(nb_ctx *c, const double *u, double *w, int mode);
+bool df_supported(int n);
+nb_status launch_dssum_sc(nb_ctx *c, double *w, const CgScalars *sc);
+nb_status launch_mask_sc(nb_ctx *c, double *w, const CgScalars *sc);
+
+constexpr int kRedThreads = 256;
+
+static int red_grid(const nb_ctx *c) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+    }
+    int64_t g = c->m.E;
+    const int64_t cap = (int64_t)sms * 4;
+    return (int)(g < cap ? g : cap);
+}
+
+// Fixed-order CTA sum; result valid in thread 0.  Uses `red` (32 doubles).
+__device__ __forceinline__ double block_sum(double v, double *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    v = (threadIdx.x < (blockDim.x >> 5)) ? red[lane] : 0.0;
+    if (wid == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+// Publishes this CTA's NV partial sums; returns true in every thread of the
+// last CTA, whose thread 0 then holds the fixed-order totals in tot[].
+template <int NV>
+__device__ bool last_block_reduce(const double (&v)[NV], double *partials, CgScalars *sc,
+                                  double (&tot)[NV]) {
+    __shared__ double red[32];
+    __shared__ int s_last;
+    double b[NV];
+#pragma unroll
+    for (int q = 0; q < NV; q++) b[q] = block_sum(v[q], red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; q++) partials[q * gridDim.x + blockIdx.x] = b[q];
+        __threadfence();
+        const unsigned t = atomicAdd(&sc->ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+        double acc = 0.0;
+        for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x)
+            acc += __ldcg(partials + q * gridDim.x + k);
+        tot[q] = block_sum(acc, red);
+    }
+    if (threadIdx.x == 0) sc->ticket = 0;
+    return true;
+}
+
+// Copies of local point (i,j,k) of element (ex,ey,ez); c = 1/mult.
+template <int N>
+__device__ __forceinline__ double inv_mult(int i, int j, int k, int ex, int ey, int ez, const Mesh &m) {
+    const int mu = mult_1d(i, ex, m.ex, N) * mult_1d(j, ey, m.ey, N) * mult_1d(k, ez, m.ez, N);
+    return mu == 1 ? 1.0 : (mu == 2 ? 0.5 : (mu == 4 ? 0.25 : 0.125));
+}
+
+// MODE 0: *out = <a,b>_c.  MODE 1 (CG): pap = <w,p>_c, alpha = rho/pap.
+// MODE 2 (CG init): r = f - w, p = 0, rho = <r,r>_c, fnorm2 = <f,f>_c.
+template <int N, int MODE>
+__global__ void __launch_bounds__(kRedThreads)
+dot_kernel(const double *__restrict__ a, const double *__restrict__ b, double *__restrict__ rr,
+           double *__restrict__ pp, Mesh m, double *partials, CgScalars *sc, double *out,
+           double *hist) {
+    constexpr int N3 = N * N * N;
+    if (MODE == 1 && sc->done) return;
+    double acc[2] = {0.0, 0.0};
+    for (int64_t e = blockIdx.x; e < m.E; e += gridDim.x) {
+        const int ex = (int)(e % m.ex), ey = (int)((e / m.ex) % m.ey),
+                  ez = (int)(e / ((int64_t)m.ex * m.ey));
+        const int64_t base = e * N3;
+        for (int p = threadIdx.x; p < N3; p += blockDim.x) {
+            const int i = p % N, j = (p / N) % N, k = p / (N * N);
+            const double cw = inv_mult<N>(i, j, k, ex, ey, ez, m);
+            if (MODE == 2) {
+                const double f = a[base + p];
+                const double r = f - b[base + p];
+                rr[base + p] = r;
+                pp[base + p] = 0.0;
+                acc[0] = fma(r * cw, r, acc[0]);
+                acc[1] = fma(f * cw, f, acc[1]);
+            } else {
+                acc[0] = fma(a[base + p] * cw, b[base + p], acc[0]);
+            }
+        }
+    }
+    double tot[2];
+    if (MODE == 2) {
+        if (!last_block_reduce<2>(acc, partials, sc, tot)) return;
+    } else {
+        double a1[1] = {acc[0]}, t1[1];
+        if (!last_block_reduce<1>(a1, partials, sc, t1)) return;
+        tot[0] = t1[0];
+    }
+    if (threadIdx.x != 0) return;
+    if (MODE == 0) {
+        *out = tot[0];
+    } else if (MODE == 1) {
+        const double pap = tot[0];
+        sc->pap = pap;
+        if (!(pap > 0.0) || !isfinite(pap)) {
+            sc->status = (int)NB_ERR_BREAKDOWN;
+            sc->done = 1;
+        } else {
+            sc->alpha = sc->rho / pap;
+        }
+    } else {
+        sc->rho = tot[0];
+        sc->rho_old = 1.0;
+        sc->fnorm2 = tot[1];
+        sc->beta = 0.0;
+        sc->it = 0;
+        sc->status = 0;
+        hist[0] = tot[0];
+        const bool conv = sc->tol > 0.0 && sqrt(tot[0]) / sqrt(tot[1]) <= sc->tol;
+        sc->done = (tot[0] == 0.0 || conv || sc->maxit == 0) ? 1 : 0;
+    }
+}
+
+// x += alpha p, r -= alpha w, rho = <r,r>_c, beta = rho/rho_old.
+template <int N>
+__global__ void __launch_bounds__(kRedThreads)
+update_kernel(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+              const double *__restrict__ w, Mesh m, double *partials, CgScalars *sc, double *hist) {
+    constexpr int N3 = N * N * N;
+    if (sc->done) return;
+    const double alpha = sc->alpha;
+    double acc[1] = {0.0};
+    for (int64_t e = blockIdx.x; e < m.E; e += gridDim.x) {
+        const int ex = (int)(e % m.ex), ey = (int)((e / m.ex) % m.ey),
+                  ez = (int)(e / ((int64_t)m.ex * m.ey));
+        const int64_t base = e * N3;
+        for (int q = threadIdx.x; q < N3; q += blockDim.x) {
+            const int i = q % N, j = (q / N) % N, k = q / (N * N);
+            const double cw = inv_mult<N>(i, j, k, ex, ey, ez, m);
+            x[base + q] = fma(alpha, p[base + q], x[base + q]);
+            const double rn = fma(-alpha, w[base + q], r[base + q]);
+            r[base + q] = rn;
+            acc[0] = fma(rn * cw, rn, acc[0]);
+        }
+    }
+    double tot[1];
+    if (!last_block_reduce<1>(acc, partials, sc, tot)) return;
+    if (threadIdx.x != 0) return;
+    const double rho = tot[0];
+    sc->rho_old = sc->rho;
+    sc->rho = rho;
+    sc->beta = rho / sc->rho_old;
+    const int it = sc->it + 1;
+    sc->it = it;
+    hist[it] = rho;
+    const bool conv = sc->tol > 0.0 && sqrt(rho) / sqrt(sc->fnorm2) <= sc->tol;
+    if (rho == 0.0 || conv || it >= sc->maxit) sc->done = 1;
+}
+
+// ---------------------------------------------------------------- host side
+template <int N>
+static void dot_launch(nb_ctx *c, int mode, const double *a, const double *b, double *out) {
+    const int grid = red_grid(c);
+    if (mode == 0)
+        dot_kernel<N, 0><<<grid, kRedThreads, 0, c->stream>>>(a, b, nullptr, nullptr, c->m, c->d_partials,
+                                                             c->d_sc, out, nullptr);
+    else if (mode == 1)
+        dot_kernel<N, 1><<<grid, kRedThreads, 0, c->stream>>>(c->d_w, c->d_p, nullptr, nullptr, c->m,
+                                                             c->d_partials, c->d_sc, nullptr, nullptr);
+    else
+        dot_kernel<N, 2><<<grid, kRedThreads, 0, c->stream>>>(a, b, c->d_r, c->d_p, c->m, c->d_partials,
+                                                             c->d_sc, nullptr, c->d_hist);
+}
+
+template <int N>
+static void update_launch(nb_ctx *c) {
+    update_kernel<N><<<red_grid(c), kRedThreads, 0, c->stream>>>(c->d_x, c->d_r, c->d_p, c->d_w, c->m,
+                                                                c->d_partials, c->d_sc, c->d_hist);
+}
+
+#define NB_DISPATCH_N(n, CALL)                                                              \
+    switch (n) {                                                                            \
+        case 2: CALL(2); break; case 3: CALL(3); break; case 4: CALL(4); break;             \
+        case 5: CALL(5); break; case 6: CALL(6); break; case 7: CALL(7); break;             \
+        case 8: CALL(8); break; case 9: CALL(9); break; case 10: CALL(10); break;           \
+        case 11: CALL(11); break; case 12: CALL(12); break; case 13: CALL(13); break;       \
+        case 14: CALL(14); break; case 15: CALL(15); break; case 16: CALL(16); break;       \
+        default: break;                                                                     \
+    }
+
+static nb_status launch_dot(nb_ctx *c, int mode, const double *a, const double *b, double *out) {
+    LaunchTimer tm(c, NB_K_DOT);
+#define CALL(NN) dot_launch<NN>(c, mode, a, b, out)
+    NB_DISPATCH_N(c->m.n, CALL)
+#undef CALL
+    NB_LAUNCH_CHECK("dot_kernel");
+    return NB_OK;
+}
+
+static nb_status launch_update(nb_ctx *c) {
+    LaunchTimer tm(c, NB_K_UPDATE);
+#define CALL(NN) update_launch<NN>(c)
+    NB_DISPATCH_N(c->m.n, CALL)
+#undef CALL
+    NB_LAUNCH_CHECK("update_kernel");
+    return NB_OK;
+}
+
+nb_status launch_ax(nb_ctx *c, const double *u, double *w) {
+    const bool df = (c->ax_variant == 0 || c->ax_variant == 2) && c->d_gxyz_df && df_supported(c->m.n);
+    return df ? launch_ax_df(c, u, w, 0) : launch_ax_fp64(c, u, w, 0);
+}
+
+nb_status launch_ax_cg(nb_ctx *c) {
+    const bool df = (c->ax_variant == 0 || c->ax_variant == 2) && c->d_gxyz_df && df_supported(c->m.n);
+    return df ? launch_ax_df(c, nullptr, nullptr, 1) : launch_ax_fp64(c, nullptr, nullptr, 1);
+}
+
+nb_status ensure_cg_workspace(nb_ctx *c) {
+    if (c->d_sc) return NB_OK;
+    const size_t bytes = sizeof(double) * c->m.npts;
+    cudaError_t e;
+    double **vecs[] = {&c->d_r, &c->d_p, &c->d_w, &c->d_x};
+    for (double **v : vecs) {
+        if ((e = dev_alloc((void **)v, bytes)) != cudaSuccess) return cuda_fail(e, "alloc CG vector");
+        c->device_bytes += bytes;
+    }
+    c->partial_cap = 2 * 4096;
+    if ((e = dev_alloc((void **)&c->d_partials, sizeof(double) * c->partial_cap)) != cudaSuccess)
+        return cuda_fail(e, "alloc partials");
+    if ((e = dev_alloc((void **)&c->d_sc, sizeof(CgScalars))) != cudaSuccess)
+        return cuda_fail(e, "alloc scalars");
+    if ((e = cudaMallocHost((void **)&c->h_sc, sizeof(CgScalars))) != cudaSuccess)
+        return cuda_fail(e, "alloc pinned scalars");
+    NB_CUDA(cudaMemsetAsync(c->d_sc, 0, sizeof(CgScalars), c->stream));
+    return NB_OK;
+}
+
+static nb_status ensure_hist(nb_ctx *c, int maxit) {
+    if (c->d_hist && c->hist_cap >= maxit + 1) return NB_OK;
+    if (c->d_hist) {
+        NB_CUDA(cudaStreamSynchronize(c->stream));
+        cudaFree(c->d_hist);
+        c->d_hist = nullptr;
+    }
+    int cap = maxit + 1 < 1024 ? 1024 : maxit + 1;
+    cudaError_t e = dev_alloc((void **)&c->d_hist, sizeof(double) * cap);
+    if (e != cudaSuccess) return cuda_fail(e, "alloc history");
+    c->hist_cap = cap;
+    return NB_OK;
+}
+
+nb_status dot_c(nb_ctx *c, const double *a, const double *b, double *out_host) {
+    nb_status s = ensure_cg_workspace(c);
+    if (s != NB_OK) return s;
+    double *d_out = c->d_partials + c->partial_cap - 1;
+    if ((s = launch_dot(c, 0, a, b, d_out)) != NB_OK) return s;
+    NB_CUDA(cudaMemcpyAsync(out_host, d_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    NB_CUDA(cudaStreamSynchronize(c->stream));
+    return harvest_timing(c);
+}
+
+// One CG iteration: four kernels that all return at once when done is set.
+static nb_status enqueue_iteration(nb_ctx *c) {
+    nb_status s;
+    if ((s = launch_ax_cg(c)) != NB_OK) return s;
+    if ((s = launch_dssum_sc(c, c->d_w, c->d_sc)) != NB_OK) return s;
+    if ((s = launch_mask_sc(c, c->d_w, c->d_sc)) != NB_OK) return s;
+    if ((s = launch_dot(c, 1, nullptr, nullptr, nullptr)) != NB_OK) return s;
+    return launch_update(c);
+}
+
+static nb_status build_graph(nb_ctx *c, int chunk) {
+    if (c->cg_graph && c->cg_graph_chunk == chunk) return NB_OK;
+    if (c->cg_graph) {
+        cudaGraphExecDestroy(c->cg_graph);
+        c->cg_graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    NB_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    nb_status s = NB_OK;
+    for (int k = 0; k < chunk && s == NB_OK; k++) s = enqueue_iteration(c);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (s != NB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->cg_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    c->cg_graph_chunk = chunk;
+    return NB_OK;
+}
+
+nb_status cg_solve_fp64(nb_ctx *c, const double *f, double *x, double tol, int maxit, int *iters,
+                        double *relres) {
+    nb_status s;
+    if ((s = ensure_cg_workspace(c)) != NB_OK) return s;
+    if ((s = ensure_hist(c, maxit)) != NB_OK) return s;
+    const size_t bytes = sizeof(double) * c->m.npts;
+    // scalars: tolerance and iteration limit; the rest is set by the init step
+    CgScalars init{};
+    init.tol = tol;
+    init.maxit = maxit;
+    *c->h_sc = init;
+    NB_CUDA(cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(CgScalars), cudaMemcpyHostToDevice, c->stream));
+    // x_int = x0; w = A x0; r = f - w; p = 0; rho, <f,f>_c
+    NB_CUDA(cudaMemcpyAsync(c->d_x, x, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if ((s = launch_ax(c, c->d_x, c->d_w)) != NB_OK) return s;
+    if ((s = launch_dssum_sc(c, c->d_w, nullptr)) != NB_OK) return s;
+    if ((s = launch_mask_sc(c, c->d_w, nullptr)) != NB_OK) return s;
+    if ((s = launch_dot(c, 2, f, c->d_w, nullptr)) != NB_OK) return s;
+
+    // Stream capture needs a non-default stream; timing needs plain launches.
+    const bool use_graph = c->stream != nullptr && !c->timing;
+    const int chunk = 16;
+    int launched = 0;
+    while (launched < maxit) {
+        if (use_graph) {
+            if ((s = build_graph(c, chunk)) != NB_OK) return s;
+            NB_CUDA(cudaGraphLaunch(c->cg_graph, c->stream));
+            launched += chunk;
+        } else {
+            for (int k = 0; k < chunk && launched < maxit; k++, launched++)
+                if ((s = enqueue_iteration(c)) != NB_OK) return s;
+        }
+        if (tol > 0.0 && launched < maxit) {
+            NB_CUDA(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream));
+            NB_CUDA(cudaStreamSynchronize(c->stream));
+            if (c->h_sc->done) break;
+        }
+    }
+    NB_CUDA(cudaMemcpyAsync(x, c->d_x, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    NB_CUDA(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream));
+    NB_CUDA(cudaStreamSynchronize(c->stream));
+    if ((s = harvest_timing(c)) != NB_OK) return s;
+    const CgScalars &h = *c->h_sc;
+    c->last_iters = h.it;
+    if (iters) *iters = h.it;
+    const double rel = h.fnorm2 > 0.0 ? sqrt(h.rho) / sqrt(h.fnorm2) : 0.0;
+    if (relres) *relres = rel;
+    if (h.status == (int)NB_ERR_BREAKDOWN) return fail(NB_ERR_BREAKDOWN, "CG breakdown: <Ap,p>_c <= 0 or not finite");
+    if (tol > 0.0 && !(rel <= tol) && h.rho != 0.0)
+        return fail(NB_ERR_NOT_CONVERGED, "CG did not reach the tolerance within maxit");
+    return NB_OK;
+}
+
+}  // namespace nekgb

@@ -1,0 +1,154 @@
+// Internal declarations shared by the CUDA sources of libnekgb.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/nekgb.h"
+
+namespace nekgb {
+
+constexpr int kMaxN = 16;
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+nb_status fail(nb_status s, const std::string &msg);
+nb_status cuda_fail(cudaError_t e, const char *what);
+
+#define NB_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return ::nekgb::cuda_fail(_e, #call);    \
+    } while (0)
+
+#define NB_LAUNCH_CHECK(what)                                           \
+    do {                                                                \
+        cudaError_t _e = cudaGetLastError();                            \
+        if (_e != cudaSuccess) return ::nekgb::cuda_fail(_e, what);     \
+    } while (0)
+
+// Device allocation with host-side fault injection: NEKGB_FAIL_ALLOC=k
+// makes the k-th allocation of the process (1-based) fail, so failure
+// paths can be tested without touching the GPU.
+cudaError_t dev_alloc(void **p, size_t bytes);
+
+// ---------------------------------------------------------------- mesh
+// Everything a kernel needs to know about the box topology.
+struct Mesh {
+    int ex, ey, ez, n;
+    int64_t E, npts;
+    int64_t NX, NY, NZ;
+};
+
+// ---------------------------------------------------------------- CG state
+// Device-resident scalars of one CG solve.
+struct CgScalars {
+    double rho;        // <r,r>_c of the current residual
+    double rho_old;    // previous rho
+    double alpha, beta;
+    double pap;        // <w,p>_c
+    double fnorm2;     // <f,f>_c
+    double tol;        // relative tolerance (<= 0: fixed iterations)
+    int it;            // iterations completed
+    int maxit;
+    int done;          // 1: no further iteration runs
+    int status;        // 0 ok, NB_ERR_BREAKDOWN
+    unsigned int ticket;  // last-block-done counter for reductions
+    int pad;
+};
+
+struct TimingRec {
+    int kid;
+    cudaEvent_t a, b;
+};
+
+}  // namespace nekgb
+
+struct nb_ctx {
+    nekgb::Mesh m;
+    nb_precision prec;
+    cudaStream_t stream;
+    int ax_variant;       // 0 auto, 1 fp64, 2 double-float
+    double D_host[nekgb::kMaxN * nekgb::kMaxN];
+    // operator data
+    double *d_D = nullptr;      // n*n, D[i*n+l]
+    double *d_gxyz = nullptr;   // [E][6][n^3]
+    uint8_t *d_mask = nullptr;  // [E][n^3] or null (box mask)
+    float *d_Df = nullptr;      // D as double-float pairs / fp32 (2*n*n)
+    float2 *d_gxyz_df = nullptr;  // [E][6][n^3] (hi,lo) pairs for double-float ax
+    float *d_gxyz32 = nullptr;  // [E][6][n^3] fp32 for the mixed inner solve
+    // CG workspace
+    double *d_r = nullptr, *d_p = nullptr, *d_w = nullptr, *d_x = nullptr;
+    double *d_partials = nullptr;
+    int partial_cap = 0;
+    nekgb::CgScalars *d_sc = nullptr;
+    nekgb::CgScalars *h_sc = nullptr;   // pinned mirror
+    double *d_hist = nullptr;
+    int hist_cap = 0;
+    int last_iters = 0;
+    // mixed precision workspace
+    float *d_r32 = nullptr, *d_p32 = nullptr, *d_w32 = nullptr, *d_z32 = nullptr;
+    // CUDA graph of a chunk of FP64 CG iterations
+    cudaGraphExec_t cg_graph = nullptr;
+    int cg_graph_chunk = 0;
+    // timing
+    bool timing = false;
+    std::vector<nekgb::TimingRec> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double t_ms[NB_K_COUNT] = {0};
+    int64_t t_launch[NB_K_COUNT] = {0};
+    size_t device_bytes = 0;
+};
+
+namespace nekgb {
+
+// Event bracketing of one launch when timing is on.
+struct LaunchTimer {
+    nb_ctx *c;
+    int kid;
+    cudaEvent_t a = nullptr, b = nullptr;
+    LaunchTimer(nb_ctx *ctx, int k);
+    ~LaunchTimer();
+};
+nb_status harvest_timing(nb_ctx *c);
+
+// ---------------------------------------------------------------- kernels
+// ax_e (ax_fp64.cu / ax_df.cu)
+nb_status launch_ax(nb_ctx *c, const double *u, double *w);
+// CG fused: p = r + beta p, w = ax_e(p)   (beta from CgScalars)
+nb_status launch_ax_cg(nb_ctx *c);
+// gather-scatter (gs.cu)
+nb_status launch_dssum(nb_ctx *c, double *w, bool with_mask);
+nb_status launch_mask(nb_ctx *c, double *w);
+nb_status launch_scatter_unique(nb_ctx *c, const double *g, double *loc);
+nb_status launch_tables(nb_ctx *c, int64_t *gid, int32_t *mult, uint8_t *mask);
+// geometry (geom.cu)
+nb_status host_gll(int n, double *xi, double *w);
+nb_status host_dmat(int n, const double *xi, double *D);
+nb_status launch_box_geometry(nb_ctx *c, double amp, const double *s, int *bad_dev);
+// reductions + CG (cg.cu)
+nb_status dot_c(nb_ctx *c, const double *a, const double *b, double *out_host);
+nb_status cg_solve_fp64(nb_ctx *c, const double *f, double *x, double tol, int maxit,
+                        int *iters, double *relres);
+nb_status cg_solve_mixed(nb_ctx *c, const double *f, double *x, double tol, int maxit,
+                         int *iters, double *relres);
+nb_status ensure_cg_workspace(nb_ctx *c);
+nb_status prepare_df(nb_ctx *c);   // double-float copies of D and gxyz
+nb_status prepare_fp32(nb_ctx *c); // fp32 copy of gxyz for the mixed solve
+
+// ---------------------------------------------------------------- device helpers
+__host__ __device__ inline int mult_1d(int idx, int e, int ne, int n) {
+    // copies of a node along one direction: 2 on an interior element face
+    return ((idx == 0 && e > 0) || (idx == n - 1 && e < ne - 1)) ? 2 : 1;
+}
+
+__host__ __device__ inline int grid_blocks(int64_t work, int per_block, int cap) {
+    int64_t b = (work + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    return (int)(b < cap ? b : cap);
+}
+
+}  // namespace nekgb

@@ -1,0 +1,323 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (written here, derived in the design doc):
+* ax_e, apply, geometry: max-norm relative error <= 1e-12 (FP64 contract).
+* dssum, mask, numbering, multiplicity, scatter: exact (value equality).
+* weighted dots: relative 1e-13 (reduction order differs).
+* CG: rho history and final x relative <= 1e-8 after 100 fixed iterations
+  (CG amplifies reduction-order differences).
+"""
+import numpy as np
+import pytest
+
+from paper_2005_13425_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+AX_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def nek():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_13425_gb300 import build as b
+    b.build()
+    from paper_2005_13425_gb300 import nekgb
+    nekgb.load()
+    s = torch.cuda.Stream()
+    torch.cuda.set_stream(s)
+    return nekgb
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.current_stream().synchronize()
+    return t.cpu().numpy()
+
+
+def rel_err(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+class Ctx:
+    def __init__(self, nek, *args, box=False, **kw):
+        self.nek = nek
+        stream = torch.cuda.current_stream()
+        if box:
+            self.h = nek.nb_setup_box(*args, stream=stream, **kw)
+        else:
+            self.h = nek.nb_setup(*args, stream=stream, **kw)
+
+    def __enter__(self):
+        return self.h
+
+    def __exit__(self, *a):
+        self.nek.nb_destroy(self.h)
+
+
+def oracle_problem(oracle, dims, n, seed=0, amp=0.05):
+    return oracle.box_problem(*dims, n, amp, inputs.perturbation_coeffs(seed))
+
+
+# ------------------------------------------------------------------ ax_e
+AX_CASES = [((5, 3, 2), 2), ((5, 3, 2), 3), ((4, 3, 2), 4), ((3, 3, 2), 5), ((3, 2, 2), 6),
+            ((3, 2, 2), 7), ((3, 2, 2), 8), ((2, 2, 2), 9), ((3, 2, 2), 10), ((2, 2, 1), 11),
+            ((2, 2, 2), 12), ((2, 1, 1), 13), ((2, 1, 1), 14), ((1, 2, 1), 15), ((2, 1, 1), 16)]
+
+
+@pytest.mark.parametrize("dims,n", AX_CASES)
+@pytest.mark.parametrize("variant", [0, 1])
+def test_ax_parity(nek, oracle, dims, n, variant):
+    P = oracle_problem(oracle, dims, n)
+    u = inputs.local_field(P["E"], n, seed=n)
+    want = oracle.ax_e(P["D"], P["gxyz"], u)
+    with Ctx(nek, dims, n, P["D"], P["gxyz"]) as ctx:
+        nek.nb_set_ax_variant(ctx, variant)
+        w = torch.empty(P["E"], n ** 3, dtype=torch.float64, device="cuda")
+        nek.nb_ax(ctx, dev(u), w)
+        got = host(w)
+    assert rel_err(got, want) <= AX_TOL
+
+
+def test_ax_ragged_many_elements(nek, oracle):
+    """More elements than the grid holds at once, with a ragged last wave."""
+    dims, n = (13, 11, 7), 6
+    P = oracle_problem(oracle, dims, n, seed=4)
+    u = inputs.local_field(P["E"], n, seed=3)
+    want = oracle.ax_e(P["D"], P["gxyz"], u)
+    with Ctx(nek, dims, n, P["D"], P["gxyz"]) as ctx:
+        w = torch.empty(P["E"], n ** 3, dtype=torch.float64, device="cuda")
+        nek.nb_ax(ctx, dev(u), w)
+        assert rel_err(host(w), want) <= AX_TOL
+
+
+def test_ax_constant_nullspace(nek, oracle):
+    dims, n = (3, 3, 3), 10
+    P = oracle_problem(oracle, dims, n, seed=7)
+    with Ctx(nek, dims, n, P["D"], P["gxyz"]) as ctx:
+        w = torch.empty(P["E"], n ** 3, dtype=torch.float64, device="cuda")
+        nek.nb_ax(ctx, torch.ones(P["E"], n ** 3, dtype=torch.float64, device="cuda"), w)
+        got = host(w)
+    # absolute bound: 1e-12 * |G| |D|^2 |u|
+    bound = 1e-12 * np.abs(P["gxyz"]).max() * np.abs(P["D"]).sum(1).max() ** 2
+    assert np.abs(got).max() <= bound
+
+
+def test_full_size_geometry_and_ax_sampled(nek, oracle):
+    """E = 4096, n = 10 in the benchmark's configuration (device-built
+    geometry, automatic kernel choice), checked on sampled elements."""
+    dims, n = (16, 16, 16), 10
+    s = inputs.perturbation_coeffs(inputs.SEED_MESH)
+    P = oracle.box_problem(*dims, n, inputs.PERTURB_AMP, s)
+    E = P["E"]
+    u = inputs.local_field(E, n, seed=inputs.SEED_U)
+    rng = np.random.default_rng(123)
+    sample = np.unique(np.concatenate([[0, E - 1], rng.choice(E, 96, replace=False)]))
+    want = oracle.ax_e(P["D"], P["gxyz"][sample], u[sample])
+    with Ctx(nek, dims, n, inputs.PERTURB_AMP, s, box=True) as ctx:
+        D = nek.nb_get_operator(ctx, n)
+        g = torch.empty(E, 6, n ** 3, dtype=torch.float64, device="cuda")
+        nek.nb_get_operator(ctx, n, g)
+        w = torch.empty(E, n ** 3, dtype=torch.float64, device="cuda")
+        nek.nb_ax(ctx, dev(u), w)
+        got = host(w)[sample]
+        gd = host(g)
+    assert rel_err(D, P["D"]) <= 1e-13
+    # max-norm of the whole metric tensor: the off-diagonal factors are
+    # small differences of cofactor products and carry absolute, not
+    # relative, rounding error
+    gmax = np.abs(P["gxyz"]).max()
+    for c in range(6):
+        assert np.abs(gd[:, c] - P["gxyz"][:, c]).max() <= 1e-12 * gmax, c
+    assert rel_err(got, want) <= AX_TOL
+
+
+# ------------------------------------------------------------------ dssum/mask
+GS_CASES = [((3, 2, 2), 4), ((4, 3, 5), 5), ((2, 2, 2), 2), ((1, 1, 1), 6), ((1, 3, 1), 3),
+            ((5, 1, 2), 8), ((16, 16, 16), 10)]
+
+
+@pytest.mark.parametrize("dims,n", GS_CASES)
+def test_dssum_mask_tables_exact(nek, oracle, dims, n):
+    E = dims[0] * dims[1] * dims[2]
+    rng = np.random.default_rng(n)
+    w = rng.uniform(-1, 1, (E, n ** 3)) * 10.0 ** rng.integers(-6, 6, (E, n ** 3))
+    D = np.eye(n)
+    g = np.zeros((E, 6, n ** 3))
+    with Ctx(nek, dims, n, D, g) as ctx:
+        wd = dev(w)
+        nek.nb_dssum(ctx, wd)
+        got = host(wd)
+        nek.nb_mask(ctx, wd)
+        got_m = host(wd)
+        gid = torch.empty(E, n ** 3, dtype=torch.int64, device="cuda")
+        mult = torch.empty(E, n ** 3, dtype=torch.int32, device="cuda")
+        msk = torch.empty(E, n ** 3, dtype=torch.uint8, device="cuda")
+        nek.nb_tables(ctx, gid, mult, msk)
+        gid, mult, msk = host(gid), host(mult), host(msk)
+    want = oracle.dssum(*dims, n, w)
+    assert np.array_equal(got, want)
+    omask = oracle.mask(*dims, n)
+    assert np.array_equal(got_m, oracle.apply_mask(omask, want))
+    assert np.array_equal(gid, oracle.gid(*dims, n))
+    assert np.array_equal(mult, oracle.multiplicity(*dims, n))
+    assert np.array_equal(msk, omask)
+
+
+def test_custom_mask_and_scatter(nek, oracle):
+    dims, n = (3, 2, 2), 5
+    E = 12
+    rng = np.random.default_rng(1)
+    cm = (rng.uniform(size=(E, n ** 3)) > 0.3).astype(np.uint8)
+    w = rng.uniform(-1, 1, (E, n ** 3))
+    with Ctx(nek, dims, n, np.eye(n), np.zeros((E, 6, n ** 3)), mask=cm) as ctx:
+        wd = dev(w)
+        nek.nb_mask(ctx, wd)
+        assert np.array_equal(host(wd), oracle.apply_mask(cm, w))
+        fu = inputs.unique_field(*dims, n, seed=5)
+        loc = torch.empty(E, n ** 3, dtype=torch.float64, device="cuda")
+        nek.nb_scatter_unique(ctx, dev(fu), loc)
+        assert np.array_equal(host(loc), oracle.scatter_unique(*dims, n, fu))
+        msk = torch.empty(E, n ** 3, dtype=torch.uint8, device="cuda")
+        nek.nb_tables(ctx, mask=msk)
+        assert np.array_equal(host(msk), cm)
+
+
+def test_apply_and_dot(nek, oracle):
+    dims, n = (4, 3, 3), 8
+    P = oracle_problem(oracle, dims, n, seed=2)
+    u = inputs.local_field(P["E"], n, seed=8)
+    want = oracle.apply_A(*dims, n, P["D"], P["gxyz"], P["mask"], u)
+    with Ctx(nek, dims, n, P["D"], P["gxyz"]) as ctx:
+        w = torch.empty_like(dev(u))
+        ud = dev(u)
+        nek.nb_apply(ctx, ud, w)
+        got = host(w)
+        d = nek.nb_dot_c(ctx, ud, w)
+    assert rel_err(got, want) <= AX_TOL
+    dw = oracle.dot_c(*dims, n, u, want)
+    assert abs(d - dw) <= 1e-12 * abs(dw)
+
+
+# ------------------------------------------------------------------ CG
+def cg_inputs(oracle, dims, n, seed_mesh=0, seed_f=1):
+    P = oracle_problem(oracle, dims, n, seed=seed_mesh)
+    f = oracle.apply_mask(P["mask"], oracle.scatter_unique(*dims, n, inputs.unique_field(*dims, n, seed=seed_f)))
+    return P, f
+
+
+def test_cg_fixed_100_iterations_config1(nek, oracle):
+    """4x4x4 elements, n = 8, 100 CG iterations (the paper's run length)."""
+    dims, n = (4, 4, 4), 8
+    P, f = cg_inputs(oracle, dims, n)
+    x_ref, it_ref, rr_ref, hist_ref, st = oracle.cg(*dims, n, P["D"], P["gxyz"], P["mask"], f,
+                                                    tol=0.0, maxit=100)
+    assert st == 0 and it_ref == 100
+    with Ctx(nek, dims, n, P["D"], P["gxyz"]) as ctx:
+        x = torch.zeros(P["E"], n ** 3, dtype=torch.float64, device="cuda")
+        st, it, rr = nek.nb_cg_solve(ctx, dev(f), x, tol=0.0, maxit=100)
+        xg = host(x)
+        hist = nek.nb_cg_history(ctx)
+    assert it == 100
+    assert np.abs(hist - hist_ref).max() / hist_ref.max() <= 1e-8
+    assert np.all(np.abs(hist / hist_ref - 1) <= 1e-6)
+    assert rel_err(xg, x_ref) <= 1e-8
+    assert abs(rr - rr_ref) <= 1e-8 * max(rr_ref, 1e-300) + 1e-14
+
+
+def test_cg_tolerance_and_determinism(nek, oracle):
+    dims, n = (3, 2, 2), 6
+    P, f = cg_inputs(oracle, dims, n, seed_mesh=3, seed_f=4)
+    x_ref, it_ref, rr_ref, _, _ = oracle.cg(*dims, n, P["D"], P["gxyz"], P["mask"], f, tol=1e-10, maxit=5000)
+    with Ctx(nek, dims, n, P["D"], P["gxyz"]) as ctx:
+        outs = []
+        for rep in range(2):
+            x = torch.zeros(P["E"], n ** 3, dtype=torch.float64, device="cuda")
+            st, it, rr = nek.nb_cg_solve(ctx, dev(f), x, tol=1e-10, maxit=5000)
+            outs.append((host(x), it, rr, nek.nb_cg_history(ctx)))
+    (x0, it0, rr0, h0), (x1, it1, rr1, h1) = outs
+    assert np.array_equal(x0, x1) and it0 == it1 and np.array_equal(h0, h1)   # deterministic
+    assert rr0 <= 1e-10 and abs(it0 - it_ref) <= 2
+    assert rel_err(x0, x_ref) <= 1e-8
+
+
+def test_cg_graph_and_plain_launch_agree(nek, oracle):
+    """The default stream cannot be captured, so it runs plain launches;
+    both paths must give bitwise-equal iterates."""
+    dims, n = (2, 2, 3), 5
+    P, f = cg_inputs(oracle, dims, n)
+    res = []
+    for stream in (torch.cuda.current_stream(), torch.cuda.default_stream()):
+        with torch.cuda.stream(stream):
+            h = nek.nb_setup(dims, n, P["D"], P["gxyz"], stream=stream)
+            x = torch.zeros(P["E"], n ** 3, dtype=torch.float64, device="cuda")
+            nek.nb_cg_solve(h, dev(f), x, tol=0.0, maxit=37)
+            stream.synchronize()
+            res.append(x.cpu().numpy())
+            nek.nb_destroy(h)
+    assert np.array_equal(res[0], res[1])
+
+
+def test_cg_edge_cases(nek, oracle):
+    dims, n = (2, 2, 2), 4
+    P, f = cg_inputs(oracle, dims, n)
+    E = P["E"]
+    with Ctx(nek, dims, n, P["D"], P["gxyz"]) as ctx:
+        x = torch.zeros(E, n ** 3, dtype=torch.float64, device="cuda")
+        st, it, rr = nek.nb_cg_solve(ctx, dev(f), x, tol=0.0, maxit=0)
+        assert it == 0 and torch.count_nonzero(x) == 0 and abs(rr - 1.0) < 1e-15
+        st, it, rr = nek.nb_cg_solve(ctx, torch.zeros_like(x), x, tol=1e-8, maxit=10)
+        assert it == 0 and rr == 0.0
+        st, it, rr = nek.nb_cg_solve(ctx, dev(f), x, tol=1e-15, maxit=3, allow=(nek.NB_ERR_NOT_CONVERGED,))
+        assert st == nek.NB_ERR_NOT_CONVERGED and it == 3
+    # a negative-definite operator makes <Ap,p>_c < 0 in the first iteration
+    with Ctx(nek, dims, n, P["D"], -P["gxyz"]) as ctx:
+        x = torch.zeros(E, n ** 3, dtype=torch.float64, device="cuda")
+        st, it, rr = nek.nb_cg_solve(ctx, dev(f), x, tol=0.0, maxit=10, allow=(nek.NB_ERR_BREAKDOWN,))
+        assert st == nek.NB_ERR_BREAKDOWN and it == 0 and torch.count_nonzero(x) == 0
+
+
+def test_cg_manufactured_solution(nek, oracle):
+    dims, n = (2, 2, 2), 7
+    P = oracle_problem(oracle, dims, n, seed=1)
+    xyz = P["xyz"]
+    us = np.sin(np.pi * xyz[:, 0]) * np.sin(np.pi * xyz[:, 1]) * np.sin(np.pi * xyz[:, 2])
+    us = oracle.apply_mask(P["mask"], us)
+    f = oracle.apply_A(*dims, n, P["D"], P["gxyz"], P["mask"], us)
+    with Ctx(nek, dims, n, P["D"], P["gxyz"]) as ctx:
+        x = torch.zeros_like(dev(f))
+        st, it, rr = nek.nb_cg_solve(ctx, dev(f), x, tol=1e-12, maxit=3000)
+        assert rr <= 1e-12
+        assert np.abs(host(x) - us).max() < 1e-8
+
+
+def test_cg_host_buffers_and_timing(nek, oracle):
+    dims, n = (3, 3, 2), 6
+    P, f = cg_inputs(oracle, dims, n)
+    with Ctx(nek, dims, n, P["D"], P["gxyz"]) as ctx:
+        x = torch.zeros(P["E"], n ** 3, dtype=torch.float64, device="cuda")
+        nek.nb_cg_solve(ctx, dev(f), x, tol=0.0, maxit=20)
+        xd = host(x)
+        xh = np.zeros_like(f)
+        nek.nb_timing_enable(ctx, True)
+        st, it, rr = nek.nb_cg_solve_host(ctx, np.ascontiguousarray(f), xh, tol=0.0, maxit=20)
+        ms, cnt = nek.nb_timing_read(ctx, nek.NB_K_AX)
+        nek.nb_timing_enable(ctx, False)
+    assert it == 20 and np.array_equal(xh, xd)
+    assert cnt == 21 and ms > 0          # 20 iterations + the initial residual
+
+
+def test_argument_errors_on_device(nek):
+    dims, n = (2, 2, 2), 4
+    with Ctx(nek, dims, n, np.eye(n), np.zeros((8, 6, n ** 3))) as ctx:
+        u = torch.zeros(8 * n ** 3 + 1, dtype=torch.float64, device="cuda")
+        with pytest.raises(nek.NekgbError) as ei:
+            nek.nb_ax(ctx, u, u)
+        assert ei.value.status == nek.NB_ERR_ARG
+        with pytest.raises(nek.NekgbError):
+            nek.nb_ax(ctx, u.data_ptr() + 4, u.data_ptr() + 8 * 4096)
