@@ -315,6 +315,11 @@ def run_gpu(args, rank, world, local):
     nekgb.nb_ax(ctx, u, w)
     t_ax = timed(lambda: nekgb.nb_ax(ctx, u, w))
     t_axds = timed(lambda: (nekgb.nb_ax(ctx, u, w), nekgb.nb_dssum(ctx, w)))
+    variant_default = nekgb.nb_get_info(ctx)["ax_variant"]
+    nekgb.nb_set_ax_variant(ctx, 1)       # native FP64 kernel, for comparison
+    nekgb.nb_ax(ctx, u, w)
+    t_ax_fp64 = timed(lambda: nekgb.nb_ax(ctx, u, w), reps=5)
+    nekgb.nb_set_ax_variant(ctx, variant_default)
 
     # ---- roofline of the dominant kernel, from the timed region's events
     hbm, _, peak_src = metrics.measured_peaks(ROOT)
@@ -364,6 +369,8 @@ def run_gpu(args, rank, world, local):
                     "hbm_frac": metrics.ax_bytes_per_point(8) * D / (t_ax * 1e-3) / 1e9 / hbm,
                     "l2": "flushed between reps"},
         "ax_dssum": {"ms": t_axds, "gdofs": D / (t_axds * 1e-3) / 1e9},
+        "ax_only_native_fp64": {"ms": t_ax_fp64, "gdofs": D / (t_ax_fp64 * 1e-3) / 1e9,
+                                "fp64_tflops": metrics.ax_flops_per_point(NGLL) * D / (t_ax_fp64 * 1e-3) / 1e12},
         "e2e": {"value": value_e2e, "unit": "GDOF/s",
                 "h2d_bytes_per_step": 2 * 8 * D, "d2h_bytes_per_step": 8 * D,
                 "api": "nb_cg_solve_host (pinned host f, x)"},

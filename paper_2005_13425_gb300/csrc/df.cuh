@@ -1,0 +1,83 @@
+// Double-float ("float-float") arithmetic on the FP32 pipes.
+//
+// A value is an unevaluated pair (h, l) of floats, |l| <= ulp(h)/2, giving a
+// 48-bit significand.  The building blocks are the classical error-free
+// transformations: Knuth's TwoSum (the exact rounding error of a + b) and the
+// FMA-based TwoProd (the exact rounding error of a * b), as used by Dekker
+// (1971) and by Ogita, Rump and Oishi's compensated dot product Dot2 (2005).
+// Every operation uses the explicit round-to-nearest intrinsics so the
+// compiler can neither contract nor reassociate them.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace nekgb {
+namespace dfa {
+
+// Compensated dot-product accumulator: s is the running FP32 sum, c the
+// running sum of every rounding error (of the products and of the sums).
+struct Acc {
+    float s, c;
+};
+
+// TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float aa = __fsub_rn(s, bb);
+    e = __fadd_rn(__fsub_rn(a, aa), __fsub_rn(b, bb));
+}
+
+// acc = (xh + xl) * (yh + yl): exact product of the high parts plus the
+// first-order cross terms (the xl*yl term is below the 48-bit precision).
+__device__ __forceinline__ Acc first(float xh, float xl, float yh, float yl) {
+    Acc a;
+    a.s = __fmul_rn(xh, yh);
+    float e = __fmaf_rn(xh, yh, -a.s);
+    e = __fmaf_rn(xh, yl, e);
+    a.c = __fmaf_rn(xl, yh, e);
+    return a;
+}
+
+// acc += (xh + xl) * (yh + yl)   (Dot2 step: TwoProd + TwoSum)
+__device__ __forceinline__ void fma(Acc &a, float xh, float xl, float yh, float yl) {
+    const float p = __fmul_rn(xh, yh);
+    float e = __fmaf_rn(xh, yh, -p);
+    e = __fmaf_rn(xh, yl, e);
+    e = __fmaf_rn(xl, yh, e);
+    float s, err;
+    two_sum(a.s, p, s, err);
+    a.s = s;
+    a.c = __fadd_rn(a.c, __fadd_rn(err, e));
+}
+
+// Normalise (Fast2Sum, valid because |c| << |s|): returns (h, l).
+__device__ __forceinline__ float2 norm(const Acc &a) {
+    const float h = __fadd_rn(a.s, a.c);
+    const float l = __fsub_rn(a.c, __fsub_rn(h, a.s));
+    return make_float2(h, l);
+}
+
+// a + b for normalised pairs (accurate: TwoSum on the high parts).
+__device__ __forceinline__ float2 add(float2 a, float2 b) {
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+    const float h = __fadd_rn(s, e);
+    const float l = __fsub_rn(e, __fsub_rn(h, s));
+    return make_float2(h, l);
+}
+
+// Split a double into a normalised pair: h = fl32(x), l = fl32(x - h).
+// x - h is exact in FP64, so h + l carries 48 bits of x.
+__device__ __forceinline__ float2 split(double x) {
+    const float h = __double2float_rn(x);
+    const float l = __double2float_rn(x - (double)h);
+    return make_float2(h, l);
+}
+
+// h + l is exact in FP64 for a normalised pair (at most 48 significant bits).
+__device__ __forceinline__ double join(float2 v) { return (double)v.x + (double)v.y; }
+
+}  // namespace dfa
+}  // namespace nekgb

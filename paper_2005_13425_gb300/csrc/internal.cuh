@@ -80,6 +80,7 @@ struct nb_ctx {
     float *d_Df = nullptr;      // D as double-float pairs / fp32 (2*n*n)
     float2 *d_gxyz_df = nullptr;  // [E][6][n^3] (hi,lo) pairs for double-float ax
     float *d_gxyz32 = nullptr;  // [E][6][n^3] fp32 for the mixed inner solve
+    int gxyz_exp = 1023;        // biased exponent of max|gxyz| (pairs are scaled by 2^-(gxyz_exp-1023))
     // CG workspace
     double *d_r = nullptr, *d_p = nullptr, *d_w = nullptr, *d_x = nullptr;
     double *d_partials = nullptr;

@@ -71,7 +71,7 @@ AX_CASES = [((5, 3, 2), 2), ((5, 3, 2), 3), ((4, 3, 2), 4), ((3, 3, 2), 5), ((3,
 
 
 @pytest.mark.parametrize("dims,n", AX_CASES)
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_ax_parity(nek, oracle, dims, n, variant):
     P = oracle_problem(oracle, dims, n)
     u = inputs.local_field(P["E"], n, seed=n)
@@ -82,6 +82,26 @@ def test_ax_parity(nek, oracle, dims, n, variant):
         nek.nb_ax(ctx, dev(u), w)
         got = host(w)
     assert rel_err(got, want) <= AX_TOL
+
+
+@pytest.mark.parametrize("scale_u,scale_g", [(1e-30, 1.0), (1e25, 1.0), (1.0, 1e-25), (1e-12, 1e20)])
+def test_ax_double_float_scale_invariance(nek, oracle, scale_u, scale_g):
+    """The FP32-pair kernel scales inputs by exact powers of two, so tiny or
+    huge data keep the same relative accuracy as data of order one."""
+    dims, n = (3, 2, 2), 10
+    P = oracle_problem(oracle, dims, n, seed=5)
+    g = P["gxyz"] * scale_g
+    u = inputs.local_field(P["E"], n, seed=6) * scale_u
+    u[1] *= 1e-6                           # elements of very different magnitude
+    want = oracle.ax_e(P["D"], g, u)
+    with Ctx(nek, dims, n, P["D"], g) as ctx:
+        nek.nb_set_ax_variant(ctx, 2)
+        w = torch.empty(P["E"], n ** 3, dtype=torch.float64, device="cuda")
+        nek.nb_ax(ctx, dev(u), w)
+        got = host(w)
+    assert rel_err(got, want) <= AX_TOL
+    # the small element is accurate relative to itself too
+    assert rel_err(got[1], want[1]) <= 1e-11
 
 
 def test_ax_ragged_many_elements(nek, oracle):
