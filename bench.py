@@ -160,16 +160,26 @@ def oracle_problem():
     return oracle, P, f
 
 
+_ORACLE_CACHE = {}
+
+
 def time_oracle_cg(iters: int):
-    """Wall time of the oracle's CG for `iters` fixed iterations."""
-    oracle, P, f = oracle_problem()
+    """Wall time of the oracle's CG for `iters` fixed iterations (the
+    problem is built once and reused)."""
+    if "p" not in _ORACLE_CACHE:
+        _ORACLE_CACHE["p"] = oracle_problem()
+    oracle, P, f = _ORACLE_CACHE["p"]
     t0 = time.perf_counter()
     _, it, _, _, _ = oracle.cg(*DIMS, NGLL, P["D"], P["gxyz"], P["mask"], f, tol=0.0, maxit=iters)
     dt = time.perf_counter() - t0
     return dt, it
 
 
-def cpu_baseline(iters: int = 4):
+def cpu_baseline(target_s: float = 15.0):
+    """The oracle's CG on the host cores, on a bounded sample of the same
+    workload: a 4-iteration probe sizes the sample to ~target_s seconds."""
+    dt0, it0 = time_oracle_cg(4)
+    iters = int(max(4, min(2000, target_s / max(dt0 / max(it0, 1), 1e-6))))
     dt, it = time_oracle_cg(iters)
     dofs = P_dofs()
     return {"value": dofs * it / dt / 1e9, "unit": "GDOF/s", "cores": hardware_threads(),
@@ -210,6 +220,49 @@ def run_reference(args, rank, world):
     }
     print(json.dumps(line))
     return 0
+
+
+# ---------------------------------------------------------------- mixed vs FP64
+def mixed_vs_fp64(nekgb, stream, n, tol=1e-10):
+    """Config 3: manufactured solution u* = sin(pi x) sin(pi y) sin(pi z) at
+    the nodes (masked), f = A u* with the FP64 operator; time to relative
+    residual `tol` with the FP64 solver and with FP32-operator defect
+    correction; error of each result against u* (the exact discrete
+    solution up to the operator's rounding)."""
+    import torch
+    E = DIMS[0] * DIMS[1] * DIMS[2]
+    s = inputs.perturbation_coeffs(inputs.SEED_MESH)
+    out = {"n": n, "E": E, "tol": tol}
+    c64 = nekgb.nb_setup_box(DIMS, n, inputs.PERTURB_AMP, s, nekgb.NB_FP64, stream)
+    cmx = nekgb.nb_setup_box(DIMS, n, inputs.PERTURB_AMP, s, nekgb.NB_MIXED, stream)
+    try:
+        xyz = torch.empty(E, 3, n ** 3, dtype=torch.float64, device="cuda")
+        nekgb.nb_box_coords(c64, xyz)
+        us = (torch.sin(torch.pi * xyz[:, 0]) * torch.sin(torch.pi * xyz[:, 1])
+              * torch.sin(torch.pi * xyz[:, 2])).contiguous()
+        nekgb.nb_mask(c64, us)
+        f = torch.empty_like(us)
+        nekgb.nb_apply(c64, us, f)
+        umax = float(us.abs().max())
+        for name, ctx in (("fp64", c64), ("mixed", cmx)):
+            x = torch.zeros_like(us)
+            nekgb.nb_cg_solve(ctx, f, x, tol=tol, maxit=20000)          # warm-up
+            x.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            stream.synchronize()
+            a.record(stream)
+            st, it, rr = nekgb.nb_cg_solve(ctx, f, x, tol=tol, maxit=20000)
+            b.record(stream)
+            b.synchronize()
+            iters, outer = nekgb.nb_solve_stats(ctx)
+            err = float((x - us).abs().max()) / umax
+            out[name] = {"ms": a.elapsed_time(b), "iterations": it, "outer": outer,
+                         "relres": rr, "max_err_vs_ustar": err}
+        out["speedup_mixed"] = out["fp64"]["ms"] / out["mixed"]["ms"]
+    finally:
+        nekgb.nb_destroy(c64)
+        nekgb.nb_destroy(cmx)
+    return out
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -376,6 +429,8 @@ def run_gpu(args, rank, world, local):
                 "api": "nb_cg_solve_host (pinned host f, x)"},
         "clocks": clocks.summary(),
     }
+    if not args.no_mixed:
+        line["mixed_vs_fp64"] = [mixed_vs_fp64(nekgb, stream, nn) for nn in (8, 10)]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     nekgb.nb_destroy(ctx)
@@ -392,6 +447,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-vs-FP64 solves")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -152,7 +152,10 @@ nb_status nb_apply(nb_ctx *ctx, const double *u_dev, double *w_dev);
  * solve is finished.  Returns NB_ERR_NOT_CONVERGED if tol > 0 was not
  * reached within maxit, NB_ERR_BREAKDOWN if <w,p>_c <= 0 or not finite
  * (x then holds the last good iterate).  For NB_MIXED contexts this runs
- * FP32-operator CG inside FP64 defect correction (see nb_mixed_solve). */
+ * FP64 defect correction around an FP32 inner CG (nb_set_mixed_params):
+ * maxit bounds the total inner iterations, *iters_out receives them, and
+ * relres is the FP64 residual sqrt(<r,r>_c/<f,f>_c) of the returned x; the
+ * mixed solve needs the box mask (NB_ERR_STATE with a mask array). */
 nb_status nb_cg_solve(nb_ctx *ctx, const double *f_dev, double *x_dev,
                       double tol, int maxit, int *iters_out, double *relres_out);
 
@@ -188,6 +191,30 @@ nb_status nb_tables(nb_ctx *ctx, int64_t *gid_dev, int32_t *mult_dev,
 /* Copy out the operator data the context holds: D_host (n*n) and/or
  * gxyz_dev (device, [E][6][n^3]).  Either may be NULL. */
 nb_status nb_get_operator(nb_ctx *ctx, double *D_host, double *gxyz_dev);
+
+/* Nodal coordinates of an nb_setup_box context: xyz_dev (device,
+ * [E][3][n^3] doubles: x, y, z per element) receives the perturbed box map
+ * at the GLL nodes.  NB_ERR_STATE for contexts built by nb_setup. */
+nb_status nb_box_coords(nb_ctx *ctx, double *xyz_dev);
+
+/* FP32 operator of the mixed-precision inner solve (NB_MIXED contexts):
+ * w = ax_e(u) with FP32 u, w and gxyz (Listing 1 in single precision).
+ * u_dev, w_dev: device, E*n^3 floats, local storage, must not overlap.
+ * NB_ERR_STATE for an NB_FP64 context. */
+nb_status nb_ax_f32(nb_ctx *ctx, const float *u_dev, float *w_dev);
+
+/* In-place FP32 dssum (sums in FP32, ascending element order). */
+nb_status nb_dssum_f32(nb_ctx *ctx, float *w_dev);
+
+/* Mixed-precision defect correction (NB_MIXED): the inner FP32 CG stops at
+ * relative residual inner_tol (default 1e-5, 0 < inner_tol < 1); at most
+ * max_outer FP64 corrections (default 50).  The outer residual, every dot
+ * product and norm, and the update x += d are FP64. */
+nb_status nb_set_mixed_params(nb_ctx *ctx, double inner_tol, int max_outer);
+
+/* Iterations of the last solve: for NB_FP64 CG iterations; for NB_MIXED
+ * the total inner iterations and the number of outer corrections. */
+nb_status nb_solve_stats(const nb_ctx *ctx, int *iters, int *outer);
 
 /* Select the ax_e kernel: 0 = automatic (fastest FP64-accurate kernel),
  * 1 = native FP64 layer kernel, 2 = double-float (FP32-pair) kernel.  All

@@ -96,6 +96,7 @@ static void free_ctx(nb_ctx *c) {
         if (p) cudaFree(p);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     if (c->cg_graph) cudaGraphExecDestroy(c->cg_graph);
+    if (c->cg_graph32) cudaGraphExecDestroy(c->cg_graph32);
     for (auto &r : c->pending) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -217,6 +218,9 @@ nb_status nb_setup_box(nb_ctx **out, nb_box mesh, int n, double amp, const doubl
     if ((e = cudaMemcpyAsync(c->d_D, c->D_host, sizeof(double) * n * n, cudaMemcpyHostToDevice,
                              c->stream)) != cudaSuccess)
         return bail(cuda_fail(e, "copy D"));
+    c->is_box = true;
+    c->box_amp = amp;
+    c->box_s[0] = s3[0]; c->box_s[1] = s3[1]; c->box_s[2] = s3[2];
     int *d_bad = nullptr;
     if ((e = dev_alloc((void **)&d_bad, sizeof(int))) != cudaSuccess) return bail(cuda_fail(e, "alloc flag"));
     cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream);
@@ -382,6 +386,49 @@ nb_status nb_get_operator(nb_ctx *c, double *D_host, double *gxyz_dev) {
                                 cudaMemcpyDeviceToDevice, c->stream));
     return NB_OK;
     NB_GUARD_END
+}
+
+nb_status nb_box_coords(nb_ctx *c, double *xyz) {
+    NB_GUARD_BEGIN
+    if (!c || !xyz) return fail(NB_ERR_ARG, "NULL argument");
+    return launch_box_coords(c, xyz);
+    NB_GUARD_END
+}
+
+nb_status nb_ax_f32(nb_ctx *c, const float *u, float *w) {
+    NB_GUARD_BEGIN
+    if (!c || !u || !w) return fail(NB_ERR_ARG, "NULL argument");
+    if (!c->d_gxyz32) return fail(NB_ERR_STATE, "the FP32 operator needs an NB_MIXED context");
+    if (((uintptr_t)u & 3u) || ((uintptr_t)w & 3u)) return fail(NB_ERR_ARG, "pointers must be 4-byte aligned");
+    const size_t bytes = sizeof(float) * c->m.npts;
+    if ((const char *)u < (const char *)w + bytes && (const char *)w < (const char *)u + bytes)
+        return fail(NB_ERR_ARG, "u and w overlap");
+    return launch_ax_f32(c, u, w, 0);
+    NB_GUARD_END
+}
+
+nb_status nb_dssum_f32(nb_ctx *c, float *w) {
+    NB_GUARD_BEGIN
+    if (!c || !w) return fail(NB_ERR_ARG, "NULL argument");
+    if (((uintptr_t)w & 3u)) return fail(NB_ERR_ARG, "w must be 4-byte aligned");
+    return launch_dssum32(c, w);
+    NB_GUARD_END
+}
+
+nb_status nb_set_mixed_params(nb_ctx *c, double inner_tol, int max_outer) {
+    if (!c) return fail(NB_ERR_ARG, "NULL context");
+    if (!(inner_tol > 0.0 && inner_tol < 1.0) || max_outer < 1)
+        return fail(NB_ERR_ARG, "need 0 < inner_tol < 1 and max_outer >= 1");
+    c->mixed_inner_tol = inner_tol;
+    c->mixed_max_outer = max_outer;
+    return NB_OK;
+}
+
+nb_status nb_solve_stats(const nb_ctx *c, int *iters, int *outer) {
+    if (!c) return fail(NB_ERR_ARG, "NULL context");
+    if (iters) *iters = c->last_iters;
+    if (outer) *outer = c->prec == NB_MIXED ? c->last_outer : 0;
+    return NB_OK;
 }
 
 nb_status nb_set_ax_variant(nb_ctx *c, int v) {

@@ -27,6 +27,7 @@
 
 #include "df.cuh"
 #include "internal.cuh"
+#include "reduce.cuh"
 
 namespace nekgb {
 
@@ -41,9 +42,13 @@ struct AxDfArgs {
     double *w;            // output (FP64, local storage)
     const double *r;      // MODE 1: residual
     double *p;            // MODE 1: search direction, updated in place
+    double *x;            // MODE 1: iterate, receives the owed x += x_alpha p
     const CgScalars *sc;  // MODE 1
-    const float2 *g;      // gxyz pairs [E][6][n^3], scaled by 2^-gexp
-    double gscale;        // 2^gexp
+    double *partials;     // MODE 1 fused: one <w,p> partial per CTA
+    int fuse;             // MODE 1: zero box-face points, interior <w,p>
+    Mesh m;
+    const float2 *g;      // gxyz pairs [E][6][n^3], scaled by 2^-(gexp-1023)
+    int gexp;             // biased exponent of max|gxyz|
     int64_t E;
 };
 
@@ -87,10 +92,12 @@ ax_df_kernel(AxDfArgs a, const __grid_constant__ DfMat<N> D) {
     double *raw = reinterpret_cast<double *>(U);
     __shared__ int s_emax;
 
-    double beta = 0.0;
+    __shared__ double red[32];
+    double beta = 0.0, xa = 0.0, dot = 0.0;
     if (MODE == 1) {
         if (a.sc->done) return;
         beta = a.sc->it == 0 ? 0.0 : a.sc->beta;
+        xa = a.sc->x_alpha;
     }
     const int t = threadIdx.x;
     if (t == 0) s_emax = 0;
@@ -103,7 +110,10 @@ ax_df_kernel(AxDfArgs a, const __grid_constant__ DfMat<N> D) {
         for (int q = t; q < N3; q += T) {
             double v;
             if (MODE == 1) {
-                v = fma(beta, a.p[eb + q], a.r[eb + q]);
+                // x += alpha p of the previous iteration, then p = r + beta p
+                const double pold = a.p[eb + q];
+                if (xa != 0.0) a.x[eb + q] = fma(xa, pold, a.x[eb + q]);
+                v = fma(beta, pold, a.r[eb + q]);
                 a.p[eb + q] = v;
             } else {
                 v = __ldg(a.u + eb + q);
@@ -117,9 +127,11 @@ ax_df_kernel(AxDfArgs a, const __grid_constant__ DfMat<N> D) {
         __syncthreads();
         int eu = s_emax;
         eu = eu < 1 ? 1 : (eu > 2046 ? 2046 : eu);
-        const double in_scale = __longlong_as_double((long long)(2046 - eu) << 52);  // 2^(1023-eu)
-        const double out_scale = __longlong_as_double((long long)eu << 52) * a.gscale; // 2^(eu-1023)*2^gexp
-        for (int q = t; q < N3; q += T) U[q] = dfa::split(raw[q] * in_scale);  // own entries only
+        // u is scaled by 2^(1023-eu) so the element's max is in [1,2); w is
+        // scaled back by 2^(eu-1023) and by the gxyz scale 2^(gexp-1023)
+        const int sh_in = 1023 - eu;
+        const int sh_out = (eu - 1023) + (a.gexp - 1023);
+        for (int q = t; q < N3; q += T) U[q] = dfa::split_scaled(raw[q], sh_in);  // own entries only
         __syncthreads();
 
         // ---- forward: wr, ws, wt along this thread's line
@@ -189,12 +201,29 @@ ax_df_kernel(AxDfArgs a, const __grid_constant__ DfMat<N> D) {
         __syncthreads();
 
         // ---- w = r-partial + s-partial + t-partial, scaled back, FP64 out
+        int ex = 0, ey = 0, ez = 0;
+        if (MODE == 1) element_coords(e, a.m, ex, ey, ez);
         for (int q = t; q < N3; q += T) {
             const float2 s = dfa::add(dfa::add(U[q], P1[q]), P2[q]);
-            a.w[eb + q] = dfa::join(s) * out_scale;
+            double wv = dfa::join_scaled(s, sh_out);
+            if (MODE == 1 && a.fuse) {
+                // Dirichlet points are zeroed before dssum (their sum is
+                // then +0, as mask-after-dssum gives); element-interior
+                // points have multiplicity 1 and are final: <w,p> here.
+                const int i = q % N, j = (q / N) % N, k = q / N2;
+                if (on_box_face(i, j, k, ex, ey, ez, a.m))
+                    wv = 0.0;
+                else if (i > 0 && i < N - 1 && j > 0 && j < N - 1 && k > 0 && k < N - 1)
+                    dot = fma(wv, a.p[eb + q], dot);
+            }
+            a.w[eb + q] = wv;
         }
         if (t == 0) s_emax = 0;
         __syncthreads();
+    }
+    if (MODE == 1 && a.fuse) {
+        const double b = block_sum(dot, red);
+        if (t == 0) a.partials[blockIdx.x] = b;
     }
 }
 
@@ -262,7 +291,7 @@ static nb_status launch_df_n(nb_ctx *c, const double *u, double *w, int mode) {
     }
     AxDfArgs args{};
     args.g = c->d_gxyz_df;
-    args.gscale = ldexp(1.0, c->gxyz_exp - 1023);
+    args.gexp = c->gxyz_exp;
     args.E = c->m.E;
     if (mode == 0) {
         args.u = u;
@@ -270,9 +299,13 @@ static nb_status launch_df_n(nb_ctx *c, const double *u, double *w, int mode) {
     } else {
         args.r = c->d_r;
         args.p = c->d_p;
+        args.x = c->d_x;
         args.w = c->d_w;
         args.sc = c->d_sc;
+        args.partials = c->d_partials;
+        args.fuse = c->fused_cg ? 1 : 0;
     }
+    args.m = c->m;
     auto kern = mode == 0 ? ax_df_kernel<N, 0> : ax_df_kernel<N, 1>;
     if (!configured[mode]) {
         NB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -282,6 +315,7 @@ static nb_status launch_df_n(nb_ctx *c, const double *u, double *w, int mode) {
     if (occ < 1) occ = 1;
     const int64_t cap = (int64_t)sms * occ;
     const int grid = (int)(c->m.E < cap ? c->m.E : cap);
+    if (mode == 1) c->ax_grid = grid;
     LaunchTimer tm(c, NB_K_AX);
     kern<<<grid, T, smem, c->stream>>>(args, D);
     NB_LAUNCH_CHECK("ax_df_kernel");

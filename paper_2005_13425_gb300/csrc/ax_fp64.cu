@@ -15,6 +15,7 @@
 // the FP64 pipe, not by HBM; the double-float kernel (ax_df.cu) is the fast
 // FP64-accurate path.  This one is kept as the plain-arithmetic variant.
 #include "internal.cuh"
+#include "reduce.cuh"
 
 namespace nekgb {
 
@@ -26,20 +27,33 @@ struct AxFp64Smem {
     double us[2][N * N];
 };
 
+struct AxCgArgs {
+    const double *r;      // residual
+    double *p;            // search direction, updated in place
+    double *x;            // iterate, receives the owed x += x_alpha p
+    const CgScalars *sc;
+    double *partials;     // fused: one <w,p> partial per CTA
+    int fuse;             // zero box-face points and sum <w,p> over interior points
+    Mesh m;
+};
+
 // MODE 0: w = ax_e(u).
-// MODE 1: CG fused, pv = r + beta*pv (written back), w = ax_e(pv).
+// MODE 1: CG iteration head: x += x_alpha p, p = r + beta p (written back),
+//         w = ax_e(p); when fused, box-face points of w are zeroed and the
+//         element-interior part of <w,p> is reduced per CTA.
 template <int N, int MODE>
 __global__ void __launch_bounds__(((N * N + 31) / 32) * 32)
 ax_fp64_kernel(const double *__restrict__ u, double *__restrict__ w,
                const double *__restrict__ gxyz, const double *__restrict__ Dg, int64_t E,
-               const double *__restrict__ r, double *__restrict__ pv,
-               const CgScalars *__restrict__ sc) {
+               AxCgArgs cg) {
     constexpr int N2 = N * N, N3 = N * N * N;
     __shared__ AxFp64Smem<N> sm;
-    double beta = 0.0;
+    __shared__ double red[32];
+    double beta = 0.0, xa = 0.0, dot = 0.0;
     if (MODE == 1) {
-        if (sc->done) return;
-        beta = sc->it == 0 ? 0.0 : sc->beta;
+        if (cg.sc->done) return;
+        beta = cg.sc->it == 0 ? 0.0 : cg.sc->beta;
+        xa = cg.sc->x_alpha;
     }
     const int t = threadIdx.x;
     const bool act = t < N2;
@@ -56,8 +70,10 @@ ax_fp64_kernel(const double *__restrict__ u, double *__restrict__ w,
         for (int q = t; q < N3; q += blockDim.x) {
             double v;
             if (MODE == 1) {
-                v = fma(beta, pv[base + q], r[base + q]);
-                pv[base + q] = v;
+                const double pold = cg.p[base + q];
+                if (xa != 0.0) cg.x[base + q] = fma(xa, pold, cg.x[base + q]);
+                v = fma(beta, pold, cg.r[base + q]);
+                cg.p[base + q] = v;
             } else {
                 v = __ldg(u + base + q);
             }
@@ -108,9 +124,24 @@ ax_fp64_kernel(const double *__restrict__ u, double *__restrict__ w,
             wcol[k] += acc;
         }
         if (act) {
+            int ex = 0, ey = 0, ez = 0;
+            if (MODE == 1) element_coords(e, cg.m, ex, ey, ez);
 #pragma unroll
-            for (int m = 0; m < N; m++) w[base + i + N * (j + N * m)] = wcol[m];
+            for (int m = 0; m < N; m++) {
+                double wv = wcol[m];
+                if (MODE == 1 && cg.fuse) {
+                    if (on_box_face(i, j, m, ex, ey, ez, cg.m))
+                        wv = 0.0;
+                    else if (i > 0 && i < N - 1 && j > 0 && j < N - 1 && m > 0 && m < N - 1)
+                        dot = fma(wv, cg.p[base + i + N * (j + N * m)], dot);
+                }
+                w[base + i + N * (j + N * m)] = wv;
+            }
         }
+    }
+    if (MODE == 1 && cg.fuse) {
+        const double b = block_sum(dot, red);
+        if (t == 0) cg.partials[blockIdx.x] = b;
     }
 }
 
@@ -127,13 +158,22 @@ static nb_status launch_n(nb_ctx *c, const double *u, double *w, int mode) {
     if (occ < 1) occ = 1;
     const int64_t cap = (int64_t)sms * occ;
     const int grid = (int)(c->m.E < cap ? c->m.E : cap);
+    AxCgArgs cg{};
+    cg.m = c->m;
     LaunchTimer tm(c, NB_K_AX);
-    if (mode == 0)
-        ax_fp64_kernel<N, 0><<<grid, threads, 0, c->stream>>>(u, w, c->d_gxyz, c->d_D, c->m.E,
-                                                              nullptr, nullptr, nullptr);
-    else
+    if (mode == 0) {
+        ax_fp64_kernel<N, 0><<<grid, threads, 0, c->stream>>>(u, w, c->d_gxyz, c->d_D, c->m.E, cg);
+    } else {
+        cg.r = c->d_r;
+        cg.p = c->d_p;
+        cg.x = c->d_x;
+        cg.sc = c->d_sc;
+        cg.partials = c->d_partials;
+        cg.fuse = c->fused_cg ? 1 : 0;
+        c->ax_grid = grid;
         ax_fp64_kernel<N, 1><<<grid, threads, 0, c->stream>>>(nullptr, c->d_w, c->d_gxyz, c->d_D,
-                                                              c->m.E, c->d_r, c->d_p, c->d_sc);
+                                                              c->m.E, cg);
+    }
     NB_LAUNCH_CHECK("ax_fp64_kernel");
     return NB_OK;
 }

@@ -4,15 +4,23 @@
 // deterministic weighted inner product <a,b>_c = sum a*b/multiplicity.
 //
 // Every scalar of the iteration (rho, alpha, beta, <w,p>_c) lives on the
-// device.  Reductions are two-level and deterministic: each CTA reduces a
-// fixed slice of the points with a fixed shuffle tree, writes one partial,
-// and the last CTA to finish (ticket counter) sums the partials in a fixed
-// order and performs the scalar step.  One iteration is four kernels
-// (ax_e fused with p = r + beta p; dssum; mask; <w,p>_c + alpha;
-// x/r update + <r,r>_c + beta), captured in chunks as a CUDA graph.
+// device and reductions are deterministic (reduce.cuh).  With the box mask
+// one iteration is three kernels:
+//   1. ax_e head: x += alpha_prev p (the x update owed by the previous
+//      iteration), p = r + beta p, w = ax_e(p), w := 0 on box faces, and
+//      the element-interior part of <w,p>_c;
+//   2. dssum of w with the shared-node part of <w,p>_c; its last CTA forms
+//      alpha = rho/<w,p>_c;
+//   3. r -= alpha w with <r,r>_c; its last CTA forms rho, beta and the
+//      convergence decision.
+// The last owed x update runs once after the loop.  With a caller-supplied
+// mask array the mask may select any point, so the iteration falls back to
+// separate dssum, mask and <w,p>_c kernels.  Chunks of iterations are
+// captured as CUDA graphs; every kernel returns at once when `done` is set.
 #include <math.h>
 
 #include "internal.cuh"
+#include "reduce.cuh"
 
 namespace nekgb {
 
@@ -20,79 +28,35 @@ nb_status launch_ax_fp64(nb_ctx *c, const double *u, double *w, int mode);
 nb_status launch_ax_df(nb_ctx *c, const double *u, double *w, int mode);
 bool df_supported(int n);
 nb_status launch_dssum_sc(nb_ctx *c, double *w, const CgScalars *sc);
+nb_status launch_dssum_cg(nb_ctx *c);
 nb_status launch_mask_sc(nb_ctx *c, double *w, const CgScalars *sc);
+int dssum_grid(const nb_ctx *c);
 
 constexpr int kRedThreads = 256;
+constexpr int kMaxRedGrid = 16384;   // partial slots reserved per reduction
 
-static int red_grid(const nb_ctx *c) {
-    static int sms = 0;
-    if (!sms) {
+static int sms() {
+    static int v = 0;
+    if (!v) {
         int dev = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms < 1) sms = 1;
-    }
-    int64_t g = c->m.E;
-    const int64_t cap = (int64_t)sms * 4;
-    return (int)(g < cap ? g : cap);
-}
-
-// Fixed-order CTA sum; result valid in thread 0.  Uses `red` (32 doubles).
-__device__ __forceinline__ double block_sum(double v, double *red) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    v = (threadIdx.x < (blockDim.x >> 5)) ? red[lane] : 0.0;
-    if (wid == 0) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (v < 1) v = 1;
     }
     return v;
 }
 
-// Publishes this CTA's NV partial sums; returns true in every thread of the
-// last CTA, whose thread 0 then holds the fixed-order totals in tot[].
-template <int NV>
-__device__ bool last_block_reduce(const double (&v)[NV], double *partials, CgScalars *sc,
-                                  double (&tot)[NV]) {
-    __shared__ double red[32];
-    __shared__ int s_last;
-    double b[NV];
-#pragma unroll
-    for (int q = 0; q < NV; q++) b[q] = block_sum(v[q], red);
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int q = 0; q < NV; q++) partials[q * gridDim.x + blockIdx.x] = b[q];
-        __threadfence();
-        const unsigned t = atomicAdd(&sc->ticket, 1u);
-        s_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return false;
-    __threadfence();
-#pragma unroll
-    for (int q = 0; q < NV; q++) {
-        double acc = 0.0;
-        for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x)
-            acc += __ldcg(partials + q * gridDim.x + k);
-        tot[q] = block_sum(acc, red);
-    }
-    if (threadIdx.x == 0) sc->ticket = 0;
-    return true;
+// Four CTAs per SM, each striding over many elements: every CTA ends with
+// one block reduction (~1.5k FP64 adds), so few, long-lived CTAs keep that
+// cost far below the per-point work on GB300's narrow FP64 pipe.
+static int red_grid(const nb_ctx *c) {
+    const int64_t cap = (int64_t)sms() * 4;
+    return (int)(c->m.E < cap ? c->m.E : cap);
 }
 
-// Copies of local point (i,j,k) of element (ex,ey,ez); c = 1/mult.
-template <int N>
-__device__ __forceinline__ double inv_mult(int i, int j, int k, int ex, int ey, int ez, const Mesh &m) {
-    const int mu = mult_1d(i, ex, m.ex, N) * mult_1d(j, ey, m.ey, N) * mult_1d(k, ez, m.ez, N);
-    return mu == 1 ? 1.0 : (mu == 2 ? 0.5 : (mu == 4 ? 0.25 : 0.125));
-}
-
-// MODE 0: *out = <a,b>_c.  MODE 1 (CG): pap = <w,p>_c, alpha = rho/pap.
-// MODE 2 (CG init): r = f - w, p = 0, rho = <r,r>_c, fnorm2 = <f,f>_c.
+// MODE 0: *out = <a,b>_c.
+// MODE 1 (unfused solver step): pap = <w,p>_c, alpha = rho/pap.
+// MODE 2 (solver start): r = f - w, p = 0, rho = <r,r>_c, fnorm2 = <f,f>_c.
 template <int N, int MODE>
 __global__ void __launch_bounds__(kRedThreads)
 dot_kernel(const double *__restrict__ a, const double *__restrict__ b, double *__restrict__ rr,
@@ -100,83 +64,90 @@ dot_kernel(const double *__restrict__ a, const double *__restrict__ b, double *_
            double *hist) {
     constexpr int N3 = N * N * N;
     if (MODE == 1 && sc->done) return;
-    double acc[2] = {0.0, 0.0};
+    double acc0 = 0.0, acc1 = 0.0;
     for (int64_t e = blockIdx.x; e < m.E; e += gridDim.x) {
-        const int ex = (int)(e % m.ex), ey = (int)((e / m.ex) % m.ey),
-                  ez = (int)(e / ((int64_t)m.ex * m.ey));
+        int ex, ey, ez;
+        element_coords(e, m, ex, ey, ez);
         const int64_t base = e * N3;
-        for (int p = threadIdx.x; p < N3; p += blockDim.x) {
+#pragma unroll 4
+        for (int p = threadIdx.x; p < N3; p += kRedThreads) {
             const int i = p % N, j = (p / N) % N, k = p / (N * N);
-            const double cw = inv_mult<N>(i, j, k, ex, ey, ez, m);
+            const double cw = inv_mult(i, j, k, ex, ey, ez, m);
             if (MODE == 2) {
                 const double f = a[base + p];
                 const double r = f - b[base + p];
                 rr[base + p] = r;
                 pp[base + p] = 0.0;
-                acc[0] = fma(r * cw, r, acc[0]);
-                acc[1] = fma(f * cw, f, acc[1]);
+                const int lg = log2_mult(i, j, k, ex, ey, ez, m);
+                acc0 = fma(scale_down_pow2(r, lg), r, acc0);
+                acc1 = fma(scale_down_pow2(f, lg), f, acc1);
             } else {
-                acc[0] = fma(a[base + p] * cw, b[base + p], acc[0]);
+                acc0 = fma(a[base + p] * cw, b[base + p], acc0);
             }
         }
     }
-    double tot[2];
     if (MODE == 2) {
-        if (!last_block_reduce<2>(acc, partials, sc, tot)) return;
-    } else {
-        double a1[1] = {acc[0]}, t1[1];
-        if (!last_block_reduce<1>(a1, partials, sc, t1)) return;
-        tot[0] = t1[0];
+        double v[2] = {acc0, acc1}, tot[2];
+        if (!last_block_reduce<2>(v, partials, gridDim.x, blockIdx.x, gridDim.x, gridDim.x,
+                                  &sc->ticket, tot))
+            return;
+        if (threadIdx.x != 0) return;
+        sc->rho = tot[0];
+        sc->rho_old = 1.0;
+        sc->fnorm2 = tot[1];
+        sc->beta = 0.0;
+        sc->x_alpha = 0.0;
+        sc->it = 0;
+        sc->status = 0;
+        if (hist) hist[0] = tot[0];
+        const bool conv = sc->tol > 0.0 && sqrt(tot[0]) / sqrt(tot[1]) <= sc->tol;
+        sc->done = (tot[0] == 0.0 || conv || sc->maxit == 0) ? 1 : 0;
+        return;
     }
+    double v[1] = {acc0}, tot[1];
+    if (!last_block_reduce<1>(v, partials, 0, blockIdx.x, gridDim.x, gridDim.x, &sc->ticket, tot))
+        return;
     if (threadIdx.x != 0) return;
     if (MODE == 0) {
         *out = tot[0];
-    } else if (MODE == 1) {
+    } else {
         const double pap = tot[0];
         sc->pap = pap;
         if (!(pap > 0.0) || !isfinite(pap)) {
             sc->status = (int)NB_ERR_BREAKDOWN;
             sc->done = 1;
+            sc->x_alpha = 0.0;
         } else {
             sc->alpha = sc->rho / pap;
+            sc->x_alpha = sc->alpha;
         }
-    } else {
-        sc->rho = tot[0];
-        sc->rho_old = 1.0;
-        sc->fnorm2 = tot[1];
-        sc->beta = 0.0;
-        sc->it = 0;
-        sc->status = 0;
-        hist[0] = tot[0];
-        const bool conv = sc->tol > 0.0 && sqrt(tot[0]) / sqrt(tot[1]) <= sc->tol;
-        sc->done = (tot[0] == 0.0 || conv || sc->maxit == 0) ? 1 : 0;
     }
 }
 
-// x += alpha p, r -= alpha w, rho = <r,r>_c, beta = rho/rho_old.
+// r -= alpha w, rho = <r,r>_c, beta = rho/rho_old, convergence decision.
 template <int N>
 __global__ void __launch_bounds__(kRedThreads)
-update_kernel(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
-              const double *__restrict__ w, Mesh m, double *partials, CgScalars *sc, double *hist) {
+update_kernel(double *__restrict__ r, const double *__restrict__ w, Mesh m, double *partials,
+              CgScalars *sc, double *hist) {
     constexpr int N3 = N * N * N;
     if (sc->done) return;
     const double alpha = sc->alpha;
-    double acc[1] = {0.0};
+    double acc = 0.0;
     for (int64_t e = blockIdx.x; e < m.E; e += gridDim.x) {
-        const int ex = (int)(e % m.ex), ey = (int)((e / m.ex) % m.ey),
-                  ez = (int)(e / ((int64_t)m.ex * m.ey));
+        int ex, ey, ez;
+        element_coords(e, m, ex, ey, ez);
         const int64_t base = e * N3;
-        for (int q = threadIdx.x; q < N3; q += blockDim.x) {
+#pragma unroll 4
+        for (int q = threadIdx.x; q < N3; q += kRedThreads) {
             const int i = q % N, j = (q / N) % N, k = q / (N * N);
-            const double cw = inv_mult<N>(i, j, k, ex, ey, ez, m);
-            x[base + q] = fma(alpha, p[base + q], x[base + q]);
             const double rn = fma(-alpha, w[base + q], r[base + q]);
             r[base + q] = rn;
-            acc[0] = fma(rn * cw, rn, acc[0]);
+            acc = fma(scale_down_pow2(rn, log2_mult(i, j, k, ex, ey, ez, m)), rn, acc);
         }
     }
-    double tot[1];
-    if (!last_block_reduce<1>(acc, partials, sc, tot)) return;
+    double v[1] = {acc}, tot[1];
+    if (!last_block_reduce<1>(v, partials, 0, blockIdx.x, gridDim.x, gridDim.x, &sc->ticket, tot))
+        return;
     if (threadIdx.x != 0) return;
     const double rho = tot[0];
     sc->rho_old = sc->rho;
@@ -189,7 +160,27 @@ update_kernel(double *__restrict__ x, double *__restrict__ r, const double *__re
     if (rho == 0.0 || conv || it >= sc->maxit) sc->done = 1;
 }
 
+// The x update owed by the last iteration: x += x_alpha p.
+__global__ void final_x_kernel(double *__restrict__ x, const double *__restrict__ p, int64_t n,
+                               const CgScalars *__restrict__ sc) {
+    const double xa = sc->x_alpha;
+    if (xa == 0.0) return;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x)
+        x[q] = fma(xa, p[q], x[q]);
+}
+
 // ---------------------------------------------------------------- host side
+#define NB_DISPATCH_N(n, CALL)                                                              \
+    switch (n) {                                                                            \
+        case 2: CALL(2); break; case 3: CALL(3); break; case 4: CALL(4); break;             \
+        case 5: CALL(5); break; case 6: CALL(6); break; case 7: CALL(7); break;             \
+        case 8: CALL(8); break; case 9: CALL(9); break; case 10: CALL(10); break;           \
+        case 11: CALL(11); break; case 12: CALL(12); break; case 13: CALL(13); break;       \
+        case 14: CALL(14); break; case 15: CALL(15); break; case 16: CALL(16); break;       \
+        default: break;                                                                     \
+    }
+
 template <int N>
 static void dot_launch(nb_ctx *c, int mode, const double *a, const double *b, double *out) {
     const int grid = red_grid(c);
@@ -201,24 +192,15 @@ static void dot_launch(nb_ctx *c, int mode, const double *a, const double *b, do
                                                              c->d_partials, c->d_sc, nullptr, nullptr);
     else
         dot_kernel<N, 2><<<grid, kRedThreads, 0, c->stream>>>(a, b, c->d_r, c->d_p, c->m, c->d_partials,
-                                                             c->d_sc, nullptr, c->d_hist);
+                                                             c->d_sc, nullptr,
+                                                             c->prec == NB_MIXED ? nullptr : c->d_hist);
 }
 
 template <int N>
 static void update_launch(nb_ctx *c) {
-    update_kernel<N><<<red_grid(c), kRedThreads, 0, c->stream>>>(c->d_x, c->d_r, c->d_p, c->d_w, c->m,
-                                                                c->d_partials, c->d_sc, c->d_hist);
+    update_kernel<N><<<red_grid(c), kRedThreads, 0, c->stream>>>(c->d_r, c->d_w, c->m, c->d_partials,
+                                                                c->d_sc, c->d_hist);
 }
-
-#define NB_DISPATCH_N(n, CALL)                                                              \
-    switch (n) {                                                                            \
-        case 2: CALL(2); break; case 3: CALL(3); break; case 4: CALL(4); break;             \
-        case 5: CALL(5); break; case 6: CALL(6); break; case 7: CALL(7); break;             \
-        case 8: CALL(8); break; case 9: CALL(9); break; case 10: CALL(10); break;           \
-        case 11: CALL(11); break; case 12: CALL(12); break; case 13: CALL(13); break;       \
-        case 14: CALL(14); break; case 15: CALL(15); break; case 16: CALL(16); break;       \
-        default: break;                                                                     \
-    }
 
 static nb_status launch_dot(nb_ctx *c, int mode, const double *a, const double *b, double *out) {
     LaunchTimer tm(c, NB_K_DOT);
@@ -238,14 +220,16 @@ static nb_status launch_update(nb_ctx *c) {
     return NB_OK;
 }
 
+static bool use_df(const nb_ctx *c) {
+    return (c->ax_variant == 0 || c->ax_variant == 2) && c->d_gxyz_df && df_supported(c->m.n);
+}
+
 nb_status launch_ax(nb_ctx *c, const double *u, double *w) {
-    const bool df = (c->ax_variant == 0 || c->ax_variant == 2) && c->d_gxyz_df && df_supported(c->m.n);
-    return df ? launch_ax_df(c, u, w, 0) : launch_ax_fp64(c, u, w, 0);
+    return use_df(c) ? launch_ax_df(c, u, w, 0) : launch_ax_fp64(c, u, w, 0);
 }
 
 nb_status launch_ax_cg(nb_ctx *c) {
-    const bool df = (c->ax_variant == 0 || c->ax_variant == 2) && c->d_gxyz_df && df_supported(c->m.n);
-    return df ? launch_ax_df(c, nullptr, nullptr, 1) : launch_ax_fp64(c, nullptr, nullptr, 1);
+    return use_df(c) ? launch_ax_df(c, nullptr, nullptr, 1) : launch_ax_fp64(c, nullptr, nullptr, 1);
 }
 
 nb_status ensure_cg_workspace(nb_ctx *c) {
@@ -257,7 +241,8 @@ nb_status ensure_cg_workspace(nb_ctx *c) {
         if ((e = dev_alloc((void **)v, bytes)) != cudaSuccess) return cuda_fail(e, "alloc CG vector");
         c->device_bytes += bytes;
     }
-    c->partial_cap = 2 * 4096;
+    // slots: up to 2 values x (ax_e CTAs + dssum CTAs, or a reduction grid)
+    c->partial_cap = 2 * (2 * kMaxRedGrid) + 16;
     if ((e = dev_alloc((void **)&c->d_partials, sizeof(double) * c->partial_cap)) != cudaSuccess)
         return cuda_fail(e, "alloc partials");
     if ((e = dev_alloc((void **)&c->d_sc, sizeof(CgScalars))) != cudaSuccess)
@@ -282,6 +267,10 @@ static nb_status ensure_hist(nb_ctx *c, int maxit) {
     return NB_OK;
 }
 
+// Solver start: r = f - w, p = 0, rho = <r,r>_c, <f,f>_c (used by the
+// mixed-precision outer loop; needs no history buffer).
+nb_status dot_start(nb_ctx *c, const double *f) { return launch_dot(c, 2, f, c->d_w, nullptr); }
+
 nb_status dot_c(nb_ctx *c, const double *a, const double *b, double *out_host) {
     nb_status s = ensure_cg_workspace(c);
     if (s != NB_OK) return s;
@@ -292,13 +281,17 @@ nb_status dot_c(nb_ctx *c, const double *a, const double *b, double *out_host) {
     return harvest_timing(c);
 }
 
-// One CG iteration: four kernels that all return at once when done is set.
+// One CG iteration; every kernel returns at once when done is set.
 static nb_status enqueue_iteration(nb_ctx *c) {
     nb_status s;
     if ((s = launch_ax_cg(c)) != NB_OK) return s;
-    if ((s = launch_dssum_sc(c, c->d_w, c->d_sc)) != NB_OK) return s;
-    if ((s = launch_mask_sc(c, c->d_w, c->d_sc)) != NB_OK) return s;
-    if ((s = launch_dot(c, 1, nullptr, nullptr, nullptr)) != NB_OK) return s;
+    if (c->fused_cg) {
+        if ((s = launch_dssum_cg(c)) != NB_OK) return s;
+    } else {
+        if ((s = launch_dssum_sc(c, c->d_w, c->d_sc)) != NB_OK) return s;
+        if ((s = launch_mask_sc(c, c->d_w, c->d_sc)) != NB_OK) return s;
+        if ((s = launch_dot(c, 1, nullptr, nullptr, nullptr)) != NB_OK) return s;
+    }
     return launch_update(c);
 }
 
@@ -330,14 +323,14 @@ nb_status cg_solve_fp64(nb_ctx *c, const double *f, double *x, double tol, int m
     nb_status s;
     if ((s = ensure_cg_workspace(c)) != NB_OK) return s;
     if ((s = ensure_hist(c, maxit)) != NB_OK) return s;
+    c->fused_cg = c->d_mask == nullptr;
     const size_t bytes = sizeof(double) * c->m.npts;
-    // scalars: tolerance and iteration limit; the rest is set by the init step
     CgScalars init{};
     init.tol = tol;
     init.maxit = maxit;
     *c->h_sc = init;
     NB_CUDA(cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(CgScalars), cudaMemcpyHostToDevice, c->stream));
-    // x_int = x0; w = A x0; r = f - w; p = 0; rho, <f,f>_c
+    // x_int = x0; w = A x0; r = f - w; p = 0; rho = <r,r>_c; <f,f>_c
     NB_CUDA(cudaMemcpyAsync(c->d_x, x, bytes, cudaMemcpyDeviceToDevice, c->stream));
     if ((s = launch_ax(c, c->d_x, c->d_w)) != NB_OK) return s;
     if ((s = launch_dssum_sc(c, c->d_w, nullptr)) != NB_OK) return s;
@@ -362,6 +355,12 @@ nb_status cg_solve_fp64(nb_ctx *c, const double *f, double *x, double tol, int m
             NB_CUDA(cudaStreamSynchronize(c->stream));
             if (c->h_sc->done) break;
         }
+    }
+    {
+        LaunchTimer tm(c, NB_K_UPDATE);
+        const int grid = grid_blocks(c->m.npts, 256, sms() * 8);
+        final_x_kernel<<<grid, 256, 0, c->stream>>>(c->d_x, c->d_p, c->m.npts, c->d_sc);
+        NB_LAUNCH_CHECK("final_x_kernel");
     }
     NB_CUDA(cudaMemcpyAsync(x, c->d_x, bytes, cudaMemcpyDeviceToDevice, c->stream));
     NB_CUDA(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream));

@@ -79,5 +79,48 @@ __device__ __forceinline__ float2 split(double x) {
 // h + l is exact in FP64 for a normalised pair (at most 48 significant bits).
 __device__ __forceinline__ double join(float2 v) { return (double)v.x + (double)v.y; }
 
+// Pair of x * 2^sh built with integer operations only (no FP64 pipe): h
+// holds the leading 24 significant bits of x (truncated), l the next 23
+// (truncated), both with x's sign; |x*2^sh - (h + l)| < 2^-46 |x*2^sh|.
+// Values whose scaled magnitude falls below 2^-126 become (0, 0): callers
+// scale so that the data's maximum is in [1, 2), which makes that an
+// absolute error below 2^-126 of the maximum.
+__device__ __forceinline__ float2 split_scaled(double x, int sh) {
+    const long long b = __double_as_longlong(x);
+    const unsigned hi32 = (unsigned)((unsigned long long)b >> 32), lo32 = (unsigned)b;
+    const unsigned sign = hi32 & 0x80000000u;
+    const int e = (int)((hi32 >> 20) & 0x7ffu);
+    const int ef = e - 1023 + sh + 127;                  // float exponent field of h
+    if (e == 0 || ef < 1) return make_float2(0.f, 0.f);
+    const unsigned mh = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
+    const float h = __uint_as_float(sign | ((unsigned)ef << 23) | mh);
+    const int el = ef - 46;                              // exponent field of the unit 2^(e-1069+sh)
+    float l = 0.f;
+    if (el >= 1) {
+        const unsigned k = (lo32 >> 6) & 0x7fffffu;      // next 23 bits as an integer
+        const float kf = __fsub_rn(__uint_as_float(0x4b000000u | k), 8388608.0f);   // exactly k
+        l = __uint_as_float(__float_as_uint(__fmul_rn(kf, __uint_as_float((unsigned)el << 23))) | sign);
+    }
+    return make_float2(h, l);
+}
+
+// f * 2^so as a double, built with integer operations (f normal or zero).
+__device__ __forceinline__ double to_double_scaled(float f, int so) {
+    const unsigned b = __float_as_uint(f);
+    const int ef = (int)((b >> 23) & 0xffu);
+    if (ef == 0) return 0.0;
+    const long long ed = (long long)(ef - 127 + 1023 + so);
+    if (ed <= 0) return 0.0;
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    if (ed >= 2047) return __longlong_as_double((long long)(sign | 0x7ff0000000000000ull));
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)ed << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+// (h + l) * 2^so in FP64: one FP64 add (exact: the pair has <= 48 bits).
+__device__ __forceinline__ double join_scaled(float2 v, int so) {
+    return __dadd_rn(to_double_scaled(v.x, so), to_double_scaled(v.y, so));
+}
+
 }  // namespace dfa
 }  // namespace nekgb

@@ -153,6 +153,42 @@ __global__ void box_geometry_kernel(double *__restrict__ gxyz, Mesh m, GeomParam
     }
 }
 
+// Nodal coordinates xyz[E][3][n^3] of the perturbed box (same map as above).
+__global__ void box_coords_kernel(double *__restrict__ xyz, Mesh m, GeomParams gp) {
+    const int n = m.n;
+    const int64_t n3 = (int64_t)n * n * n;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m.npts;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = q / n3;
+        const int p = (int)(q - e * n3);
+        const int i = p % n, j = (p / n) % n, k = p / (n * n);
+        const int ex = (int)(e % m.ex), ey = (int)((e / m.ex) % m.ey), ez = (int)(e / ((int64_t)m.ex * m.ey));
+        const double X = (ex + 0.5 * (gp.xi[i] + 1.0)) / m.ex;
+        const double Y = (ey + 0.5 * (gp.xi[j] + 1.0)) / m.ey;
+        const double Z = (ez + 0.5 * (gp.xi[k] + 1.0)) / m.ez;
+        const double bump = sin(M_PI * X) * sin(M_PI * Y) * sin(M_PI * Z);
+        double *o = xyz + e * 3 * n3 + p;
+        o[0] = X + gp.amp * gp.s[0] * bump;
+        o[n3] = Y + gp.amp * gp.s[1] * bump;
+        o[2 * n3] = Z + gp.amp * gp.s[2] * bump;
+    }
+}
+
+nb_status launch_box_coords(nb_ctx *c, double *xyz) {
+    if (!c->is_box) return fail(NB_ERR_STATE, "coordinates are known only for nb_setup_box contexts");
+    GeomParams gp;
+    nb_status st = host_gll(c->m.n, gp.xi, gp.w);
+    if (st != NB_OK) return st;
+    gp.amp = c->box_amp;
+    gp.s[0] = c->box_s[0]; gp.s[1] = c->box_s[1]; gp.s[2] = c->box_s[2];
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    box_coords_kernel<<<grid_blocks(c->m.npts, 256, sms * 8), 256, 0, c->stream>>>(xyz, c->m, gp);
+    NB_LAUNCH_CHECK("box_coords_kernel");
+    return NB_OK;
+}
+
 nb_status launch_box_geometry(nb_ctx *c, double amp, const double *s, int *bad_dev) {
     GeomParams gp;
     const int n = c->m.n;

@@ -9,102 +9,216 @@
 // copies from +0.0 in ascending element order and writes the sum back to
 // every copy, which makes the result bit-for-bit independent of the launch.
 #include "internal.cuh"
+#include "reduce.cuh"
 
 namespace nekgb {
 
 // Non-plane coordinate q (of NX - (Ex - 1)) -> global coordinate: 0, the
 // element-interior indices, and the last node.
-__device__ __forceinline__ int64_t nonplane_coord(int64_t q, int ne, int n, int64_t NG) {
+__device__ __forceinline__ int nonplane_coord(int q, int ne, int n, int NG) {
     if (q == 0) return 0;
-    const int64_t last = (int64_t)ne * (n - 2) + 1;
+    const int last = ne * (n - 2) + 1;
     if (q == last) return NG - 1;
-    const int64_t qq = q - 1;
+    const int qq = q - 1;
     return (qq / (n - 2)) * (n - 1) + 1 + qq % (n - 2);
 }
 
 // Copies of global coordinate g along one direction: up to two (element,
 // local index) pairs, in ascending element order.
-__device__ __forceinline__ int copies_1d(int64_t g, int ne, int n, int *el, int *li) {
-    const int64_t a = g / (n - 1);
-    const int64_t rem = g - a * (n - 1);
+__device__ __forceinline__ int copies_1d(int g, int ne, int n, int *el, int *li) {
+    const int a = g / (n - 1);
+    const int rem = g - a * (n - 1);
     if (rem == 0 && a > 0 && a < ne) {
-        el[0] = (int)a - 1; li[0] = n - 1;
-        el[1] = (int)a;     li[1] = 0;
+        el[0] = a - 1; li[0] = n - 1;
+        el[1] = a;     li[1] = 0;
         return 2;
     }
-    const int64_t ee = a < ne ? a : ne - 1;
-    el[0] = (int)ee;
-    li[0] = (int)(g - ee * (n - 1));
+    const int ee = a < ne ? a : ne - 1;
+    el[0] = ee;
+    li[0] = g - ee * (n - 1);
     return 1;
 }
 
-__global__ void dssum_kernel(double *__restrict__ w, Mesh m, int64_t cx, int64_t cy, int64_t cz,
-                             const CgScalars *__restrict__ sc) {
-    if (sc && sc->done) return;
+// Work item q -> global node (gx, gy, gz) with more than one copy.  The set
+// is enumerated as: nodes on interior x-planes; then nodes on interior
+// y-planes off the x-planes; then nodes on interior z-planes off both.
+__device__ __forceinline__ void shared_node(int q, const Mesh &m, int cx, int cy, int &gx, int &gy,
+                                            int &gz) {
     const int n = m.n;
-    const int64_t n3 = (int64_t)n * n * n;
-    const int64_t total = cx + cy + cz;
-    const int64_t NXp = m.NX - (m.ex - 1), NYp = m.NY - (m.ey - 1);
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t gx, gy, gz;
-        if (q < cx) {              // interior x-planes, all y, z
-            int64_t r = q;
-            gy = r % m.NY; r /= m.NY;
-            gz = r % m.NZ; r /= m.NZ;
-            gx = (r + 1) * (n - 1);
-        } else if (q < cx + cy) {  // interior y-planes, x off the x-planes
-            int64_t r = q - cx;
-            gx = nonplane_coord(r % NXp, m.ex, n, m.NX); r /= NXp;
-            gz = r % m.NZ; r /= m.NZ;
-            gy = (r + 1) * (n - 1);
-        } else {                   // interior z-planes, x and y off the planes
-            int64_t r = q - cx - cy;
-            gx = nonplane_coord(r % NXp, m.ex, n, m.NX); r /= NXp;
-            gy = nonplane_coord(r % NYp, m.ey, n, m.NY); r /= NYp;
-            gz = (r + 1) * (n - 1);
-        }
-        int elx[2], lix[2], ely[2], liy[2], elz[2], liz[2];
-        const int nx = copies_1d(gx, m.ex, n, elx, lix);
-        const int ny = copies_1d(gy, m.ey, n, ely, liy);
-        const int nz = copies_1d(gz, m.ez, n, elz, liz);
-        int64_t idx[8];
-        int c = 0;
-        for (int a = 0; a < nz; a++)
-            for (int b = 0; b < ny; b++)
-                for (int d = 0; d < nx; d++) {
-                    const int64_t e = elx[d] + (int64_t)m.ex * (ely[b] + (int64_t)m.ey * elz[a]);
-                    idx[c++] = e * n3 + lix[d] + n * (liy[b] + (int64_t)n * liz[a]);
-                }
-        double s = 0.0;
-        for (int k = 0; k < c; k++) s = __dadd_rn(s, w[idx[k]]);
-        for (int k = 0; k < c; k++) w[idx[k]] = s;
+    const int NX = (int)m.NX, NY = (int)m.NY, NZ = (int)m.NZ;
+    const int NXp = NX - (m.ex - 1), NYp = NY - (m.ey - 1);
+    if (q < cx) {
+        int r = q;
+        gy = r % NY; r /= NY;
+        gz = r % NZ; r /= NZ;
+        gx = (r + 1) * (n - 1);
+    } else if (q < cx + cy) {
+        int r = q - cx;
+        gx = nonplane_coord(r % NXp, m.ex, n, NX); r /= NXp;
+        gz = r % NZ; r /= NZ;
+        gy = (r + 1) * (n - 1);
+    } else {
+        int r = q - cx - cy;
+        gx = nonplane_coord(r % NXp, m.ex, n, NX); r /= NXp;
+        gy = nonplane_coord(r % NYp, m.ey, n, NY); r /= NYp;
+        gz = (r + 1) * (n - 1);
     }
 }
 
-// Mask: w := +0.0 at Dirichlet points.  Box mask: points whose global node
-// lies on a face of the box; otherwise the context's mask array.
-__global__ void mask_kernel(double *__restrict__ w, Mesh m, const uint8_t *__restrict__ mask,
-                            const CgScalars *__restrict__ sc) {
-    if (sc && sc->done) return;
+// Local indices of the copies of node (gx,gy,gz), ascending element order.
+__device__ __forceinline__ int node_copies(int gx, int gy, int gz, const Mesh &m, int64_t *idx) {
     const int n = m.n;
     const int64_t n3 = (int64_t)n * n * n;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m.npts;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        bool zero;
-        if (mask) {
-            zero = mask[q] == 0;
+    int elx[2], lix[2], ely[2], liy[2], elz[2], liz[2];
+    const int nx = copies_1d(gx, m.ex, n, elx, lix);
+    const int ny = copies_1d(gy, m.ey, n, ely, liy);
+    const int nz = copies_1d(gz, m.ez, n, elz, liz);
+    int c = 0;
+    for (int a = 0; a < nz; a++)
+        for (int b = 0; b < ny; b++)
+            for (int d = 0; d < nx; d++) {
+                const int64_t e = elx[d] + (int64_t)m.ex * (ely[b] + (int64_t)m.ey * elz[a]);
+                idx[c++] = e * n3 + lix[d] + n * (liy[b] + n * liz[a]);
+            }
+    return c;
+}
+
+// (+0.0) + v, computed with integer operations: -0.0 becomes +0.0.
+__device__ __forceinline__ double plus_zero(double v) {
+    return (__double_as_longlong(v) << 1) == 0 ? 0.0 : v;
+}
+__device__ __forceinline__ float plus_zero(float v) { return (__float_as_uint(v) << 1) == 0u ? 0.f : v; }
+
+// dot += s * 2^-lg * ps (the node's w times the sum of its p copies, each
+// weighted by 1/multiplicity = 2^-lg); the power-of-two scaling is exact.
+__device__ __forceinline__ double node_dot(double dot, double s, int lg, double ps) {
+    const double cinv = lg == 1 ? 0.5 : (lg == 2 ? 0.25 : 0.125);
+    return fma(s * cinv, ps, dot);
+}
+__device__ __forceinline__ double node_dot(double dot, float s, int lg, double ps) {
+    return node_dot(dot, (double)s, lg, ps);
+}
+
+// Plain dssum (CG = false) or the fused solver step (CG = true): the node
+// sums are written back and, in the solver, each shared node adds
+// w_g * sum_copies(p)/multiplicity to <w,p>_c; the last CTA adds the
+// element-interior partials left by ax_e, forms alpha = rho/<w,p>_c and
+// flags a breakdown.
+template <typename T, bool CG>
+__global__ void dssum_kernel(T *__restrict__ w, const T *__restrict__ p, Mesh m, int cx,
+                             int cy, int cz, CgScalars *sc, double *partials, int slot0) {
+    if (sc && sc->done) return;
+    const int total = cx + cy + cz;
+    double dot = 0.0;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        int gx, gy, gz;
+        shared_node(q, m, cx, cy, gx, gy, gz);
+        int64_t idx[8];
+        const int c = node_copies(gx, gy, gz, m, idx);
+        // Sum from +0.0 in ascending element order.  (+0.0) + v equals v
+        // except for v = -0.0, so the first add is a sign fix-up done with
+        // integer operations; the remaining adds are exact-count loops so no
+        // predicated-off FP64 adds are issued (GB300's FP64 pipe is narrow).
+        if (c == 2) {
+            const T a0 = w[idx[0]], a1 = w[idx[1]];
+            const T s = plus_zero(a0) + a1;
+            w[idx[0]] = s;
+            w[idx[1]] = s;
+            if (CG) dot = node_dot(dot, s, 1, (double)p[idx[0]] + (double)p[idx[1]]);
+        } else if (c == 4) {
+            T a[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) a[k] = w[idx[k]];
+            T s = plus_zero(a[0]);
+#pragma unroll
+            for (int k = 1; k < 4; k++) s = s + a[k];
+#pragma unroll
+            for (int k = 0; k < 4; k++) w[idx[k]] = s;
+            if (CG) {
+                double ps = (double)p[idx[0]];
+#pragma unroll
+                for (int k = 1; k < 4; k++) ps += (double)p[idx[k]];
+                dot = node_dot(dot, s, 2, ps);
+            }
         } else {
-            const int64_t e = q / n3;
-            const int p = (int)(q - e * n3);
-            const int i = p % n, j = (p / n) % n, k = p / (n * n);
-            const int ex = (int)(e % m.ex), ey = (int)((e / m.ex) % m.ey), ez = (int)(e / ((int64_t)m.ex * m.ey));
-            zero = (i == 0 && ex == 0) || (i == n - 1 && ex == m.ex - 1) ||
-                   (j == 0 && ey == 0) || (j == n - 1 && ey == m.ey - 1) ||
-                   (k == 0 && ez == 0) || (k == n - 1 && ez == m.ez - 1);
+            T a[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) a[k] = w[idx[k]];
+            T s = plus_zero(a[0]);
+#pragma unroll
+            for (int k = 1; k < 8; k++) s = s + a[k];
+#pragma unroll
+            for (int k = 0; k < 8; k++) w[idx[k]] = s;
+            if (CG) {
+                double ps = (double)p[idx[0]];
+#pragma unroll
+                for (int k = 1; k < 8; k++) ps += (double)p[idx[k]];
+                dot = node_dot(dot, s, 3, ps);
+            }
         }
-        if (zero) w[q] = 0.0;
     }
+    if (CG) {
+        double v[1] = {dot}, tot[1];
+        if (!last_block_reduce<1>(v, partials, 0, slot0 + blockIdx.x, slot0 + gridDim.x, gridDim.x,
+                                  &sc->ticket, tot))
+            return;
+        if (threadIdx.x != 0) return;
+        const double pap = tot[0];
+        sc->pap = pap;
+        if (!(pap > 0.0) || !isfinite(pap)) {
+            sc->status = (int)NB_ERR_BREAKDOWN;
+            sc->done = 1;
+            sc->x_alpha = 0.0;
+        } else {
+            sc->alpha = sc->rho / pap;
+            sc->x_alpha = sc->alpha;
+        }
+    }
+}
+
+// Box mask: zero every local point on a face of the box (only those points
+// are visited: two faces per direction, n^2 points per face element).
+__global__ void mask_box_kernel(double *__restrict__ w, Mesh m, const CgScalars *__restrict__ sc) {
+    if (sc && sc->done) return;
+    const int n = m.n, n2 = n * n;
+    const int64_t n3 = (int64_t)n * n * n;
+    const int fx = m.ey * m.ez * n2, fy = m.ex * m.ez * n2, fz = m.ex * m.ey * n2;
+    const int total = 2 * (fx + fy + fz);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        int ex, ey, ez, i, j, k, r;
+        if (q < 2 * fx) {
+            const int side = q / fx;
+            r = q - side * fx;
+            const int pt = r % n2, el = r / n2;
+            ey = el % m.ey; ez = el / m.ey; ex = side ? m.ex - 1 : 0;
+            j = pt % n; k = pt / n; i = side ? n - 1 : 0;
+        } else if (q < 2 * (fx + fy)) {
+            const int qq = q - 2 * fx;
+            const int side = qq / fy;
+            r = qq - side * fy;
+            const int pt = r % n2, el = r / n2;
+            ex = el % m.ex; ez = el / m.ex; ey = side ? m.ey - 1 : 0;
+            i = pt % n; k = pt / n; j = side ? n - 1 : 0;
+        } else {
+            const int qq = q - 2 * (fx + fy);
+            const int side = qq / fz;
+            r = qq - side * fz;
+            const int pt = r % n2, el = r / n2;
+            ex = el % m.ex; ey = el / m.ex; ez = side ? m.ez - 1 : 0;
+            i = pt % n; j = pt / n; k = side ? n - 1 : 0;
+        }
+        const int64_t e = ex + (int64_t)m.ex * (ey + (int64_t)m.ey * ez);
+        w[e * n3 + i + n * (j + n * k)] = 0.0;
+    }
+}
+
+// Mask from the context's array: w := +0.0 where mask == 0.
+__global__ void mask_array_kernel(double *__restrict__ w, Mesh m, const uint8_t *__restrict__ mask,
+                                  const CgScalars *__restrict__ sc) {
+    if (sc && sc->done) return;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m.npts;
+         q += (int64_t)gridDim.x * blockDim.x)
+        if (mask[q] == 0) w[q] = 0.0;
 }
 
 __global__ void scatter_unique_kernel(const double *__restrict__ g, double *__restrict__ loc, Mesh m) {
@@ -147,6 +261,7 @@ __global__ void tables_kernel(int64_t *__restrict__ gid, int32_t *__restrict__ m
     }
 }
 
+
 static int sm_count() {
     static int sms = 0;
     if (!sms) {
@@ -158,27 +273,80 @@ static int sm_count() {
     return sms;
 }
 
-nb_status launch_dssum_sc(nb_ctx *c, double *w, const CgScalars *sc) {
-    const Mesh &m = c->m;
+static void shared_counts(const Mesh &m, int &cx, int &cy, int &cz) {
     const int64_t NXp = m.NX - (m.ex - 1), NYp = m.NY - (m.ey - 1);
-    const int64_t cx = (int64_t)(m.ex - 1) * m.NY * m.NZ;
-    const int64_t cy = (int64_t)(m.ey - 1) * NXp * m.NZ;
-    const int64_t cz = (int64_t)(m.ez - 1) * NXp * NYp;
-    const int64_t total = cx + cy + cz;
-    if (total == 0) return NB_OK;
-    const int threads = 256;
-    const int grid = grid_blocks(total, threads, sm_count() * 8);
+    cx = (int)((int64_t)(m.ex - 1) * m.NY * m.NZ);
+    cy = (int)((int64_t)(m.ey - 1) * NXp * m.NZ);
+    cz = (int)((int64_t)(m.ez - 1) * NXp * NYp);
+}
+
+// Eight CTAs per SM striding over the shared nodes (one block reduction
+// per CTA in the solver step).
+int dssum_grid(const nb_ctx *c) {
+    int cx, cy, cz;
+    shared_counts(c->m, cx, cy, cz);
+    return grid_blocks((int64_t)cx + cy + cz, 256, sm_count() * 8);
+}
+
+nb_status launch_dssum_sc(nb_ctx *c, double *w, const CgScalars *sc) {
+    int cx, cy, cz;
+    shared_counts(c->m, cx, cy, cz);
+    if ((int64_t)cx + cy + cz == 0) return NB_OK;
     LaunchTimer tm(c, NB_K_DSSUM);
-    dssum_kernel<<<grid, threads, 0, c->stream>>>(w, m, cx, cy, cz, sc);
+    dssum_kernel<double, false><<<dssum_grid(c), 256, 0, c->stream>>>(
+        w, nullptr, c->m, cx, cy, cz, const_cast<CgScalars *>(sc), nullptr, 0);
     NB_LAUNCH_CHECK("dssum_kernel");
+    return NB_OK;
+}
+
+// Fused solver step: dssum of w, shared-node part of <w,p>_c, alpha.
+nb_status launch_dssum_cg(nb_ctx *c) {
+    int cx, cy, cz;
+    shared_counts(c->m, cx, cy, cz);
+    LaunchTimer tm(c, NB_K_DSSUM);
+    dssum_kernel<double, true><<<dssum_grid(c), 256, 0, c->stream>>>(c->d_w, c->d_p, c->m, cx, cy, cz,
+                                                                     c->d_sc, c->d_partials, c->ax_grid);
+    NB_LAUNCH_CHECK("dssum_kernel<cg>");
+    return NB_OK;
+}
+
+// The same fused step for the FP32 inner solve of the mixed-precision path:
+// node sums in FP32 (ascending element order), <w,p>_c in FP64.
+nb_status launch_dssum_cg32(nb_ctx *c) {
+    int cx, cy, cz;
+    shared_counts(c->m, cx, cy, cz);
+    LaunchTimer tm(c, NB_K_DSSUM);
+    dssum_kernel<float, true><<<dssum_grid(c), 256, 0, c->stream>>>(c->d_w32, c->d_p32, c->m, cx, cy, cz,
+                                                                    c->d_sc, c->d_partials, c->ax_grid);
+    NB_LAUNCH_CHECK("dssum_kernel<f32,cg>");
+    return NB_OK;
+}
+
+// Plain FP32 dssum (tests of the inner operator).
+nb_status launch_dssum32(nb_ctx *c, float *w) {
+    int cx, cy, cz;
+    shared_counts(c->m, cx, cy, cz);
+    if ((int64_t)cx + cy + cz == 0) return NB_OK;
+    LaunchTimer tm(c, NB_K_DSSUM);
+    dssum_kernel<float, false><<<dssum_grid(c), 256, 0, c->stream>>>(w, nullptr, c->m, cx, cy, cz,
+                                                                     nullptr, nullptr, 0);
+    NB_LAUNCH_CHECK("dssum_kernel<f32>");
     return NB_OK;
 }
 
 nb_status launch_mask_sc(nb_ctx *c, double *w, const CgScalars *sc) {
     const int threads = 256;
-    const int grid = grid_blocks(c->m.npts, threads, sm_count() * 8);
     LaunchTimer tm(c, NB_K_MASK);
-    mask_kernel<<<grid, threads, 0, c->stream>>>(w, c->m, c->d_mask, sc);
+    if (c->d_mask) {
+        const int grid = grid_blocks(c->m.npts, threads, sm_count() * 8);
+        mask_array_kernel<<<grid, threads, 0, c->stream>>>(w, c->m, c->d_mask, sc);
+    } else {
+        const Mesh &m = c->m;
+        const int64_t total = 2 * (int64_t)m.n * m.n * ((int64_t)m.ey * m.ez + (int64_t)m.ex * m.ez +
+                                                        (int64_t)m.ex * m.ey);
+        const int grid = grid_blocks(total, threads, sm_count() * 8);
+        mask_box_kernel<<<grid, threads, 0, c->stream>>>(w, c->m, sc);
+    }
     NB_LAUNCH_CHECK("mask_kernel");
     return NB_OK;
 }

@@ -52,6 +52,7 @@ struct CgScalars {
     double pap;        // <w,p>_c
     double fnorm2;     // <f,f>_c
     double tol;        // relative tolerance (<= 0: fixed iterations)
+    double x_alpha;    // alpha of the x update still owed to x (0: none)
     int it;            // iterations completed
     int maxit;
     int done;          // 1: no further iteration runs
@@ -80,7 +81,9 @@ struct nb_ctx {
     float *d_Df = nullptr;      // D as double-float pairs / fp32 (2*n*n)
     float2 *d_gxyz_df = nullptr;  // [E][6][n^3] (hi,lo) pairs for double-float ax
     float *d_gxyz32 = nullptr;  // [E][6][n^3] fp32 for the mixed inner solve
-    int gxyz_exp = 1023;        // biased exponent of max|gxyz| (pairs are scaled by 2^-(gxyz_exp-1023))
+    int gxyz_exp = 1023;
+    bool is_box = false;        // built by nb_setup_box (coordinates known)
+    double box_amp = 0.0, box_s[3] = {0, 0, 0};        // biased exponent of max|gxyz| (pairs are scaled by 2^-(gxyz_exp-1023))
     // CG workspace
     double *d_r = nullptr, *d_p = nullptr, *d_w = nullptr, *d_x = nullptr;
     double *d_partials = nullptr;
@@ -90,11 +93,19 @@ struct nb_ctx {
     double *d_hist = nullptr;
     int hist_cap = 0;
     int last_iters = 0;
+    int ax_grid = 0;                    // partial slots written by the fused ax_e
+    bool fused_cg = false;              // box mask: fused CG iteration
     // mixed precision workspace
     float *d_r32 = nullptr, *d_p32 = nullptr, *d_w32 = nullptr, *d_z32 = nullptr;
-    // CUDA graph of a chunk of FP64 CG iterations
+    // CUDA graphs of chunks of FP64 and FP32 (inner) CG iterations
     cudaGraphExec_t cg_graph = nullptr;
     int cg_graph_chunk = 0;
+    cudaGraphExec_t cg_graph32 = nullptr;
+    int cg_graph32_chunk = 0;
+    // mixed-precision parameters and statistics
+    double mixed_inner_tol = 1e-5;
+    int mixed_max_outer = 50;
+    int last_outer = 0;
     // timing
     bool timing = false;
     std::vector<nekgb::TimingRec> pending;
@@ -126,10 +137,14 @@ nb_status launch_dssum(nb_ctx *c, double *w, bool with_mask);
 nb_status launch_mask(nb_ctx *c, double *w);
 nb_status launch_scatter_unique(nb_ctx *c, const double *g, double *loc);
 nb_status launch_tables(nb_ctx *c, int64_t *gid, int32_t *mult, uint8_t *mask);
+// FP32 operator for the mixed-precision inner solve (ax_f32.cu, gs.cu)
+nb_status launch_ax_f32(nb_ctx *c, const float *u, float *w, int mode);
+nb_status launch_dssum32(nb_ctx *c, float *w);
 // geometry (geom.cu)
 nb_status host_gll(int n, double *xi, double *w);
 nb_status host_dmat(int n, const double *xi, double *D);
 nb_status launch_box_geometry(nb_ctx *c, double amp, const double *s, int *bad_dev);
+nb_status launch_box_coords(nb_ctx *c, double *xyz);
 // reductions + CG (cg.cu)
 nb_status dot_c(nb_ctx *c, const double *a, const double *b, double *out_host);
 nb_status cg_solve_fp64(nb_ctx *c, const double *f, double *x, double tol, int maxit,

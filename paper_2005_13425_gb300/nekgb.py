@@ -71,6 +71,11 @@ _SIGS = {
     "nb_tables": [_vp, _vp, _vp, _vp],
     "nb_get_operator": [_vp, _vp, _vp],
     "nb_set_ax_variant": [_vp, ctypes.c_int],
+    "nb_box_coords": [_vp, _vp],
+    "nb_ax_f32": [_vp, _vp, _vp],
+    "nb_dssum_f32": [_vp, _vp],
+    "nb_set_mixed_params": [_vp, ctypes.c_double, ctypes.c_int],
+    "nb_solve_stats": [_vp, _ip, _ip],
     "nb_timing_enable": [_vp, ctypes.c_int],
     "nb_timing_read": [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
 }
@@ -250,6 +255,30 @@ def nb_get_operator(ctx, n, gxyz_dev=None) -> np.ndarray:
     _check(load().nb_get_operator(ctx, D.ctypes.data, _ptr(gxyz_dev, "torch.float64")),
            "nb_get_operator")
     return D
+
+
+def nb_box_coords(ctx, xyz):
+    _check(load().nb_box_coords(ctx, _ptr(xyz, "torch.float64")), "nb_box_coords")
+
+
+def nb_ax_f32(ctx, u, w):
+    _check(load().nb_ax_f32(ctx, _ptr(u, "torch.float32"), _ptr(w, "torch.float32")), "nb_ax_f32")
+
+
+def nb_dssum_f32(ctx, w):
+    _check(load().nb_dssum_f32(ctx, _ptr(w, "torch.float32")), "nb_dssum_f32")
+
+
+def nb_set_mixed_params(ctx, inner_tol: float = 1e-5, max_outer: int = 50):
+    _check(load().nb_set_mixed_params(ctx, float(inner_tol), int(max_outer)), "nb_set_mixed_params")
+
+
+def nb_solve_stats(ctx):
+    """(iterations, outer corrections) of the last solve."""
+    it = ctypes.c_int(0)
+    outer = ctypes.c_int(0)
+    _check(load().nb_solve_stats(ctx, ctypes.byref(it), ctypes.byref(outer)), "nb_solve_stats")
+    return it.value, outer.value
 
 
 def nb_set_ax_variant(ctx, variant: int):
