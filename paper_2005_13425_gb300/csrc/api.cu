@@ -362,6 +362,24 @@ nb_status nb_dot_c(nb_ctx *c, const double *a, const double *b, double *out) {
     NB_GUARD_END
 }
 
+nb_status nb_dot_c_noalloc(nb_box mesh, int n, const double *a, const double *b, double *out,
+                           void *cuda_stream) {
+    NB_GUARD_BEGIN
+    nb_status s = check_mesh(mesh, n);
+    if (s != NB_OK) return s;
+    if (!a || !b || !out) return fail(NB_ERR_ARG, "NULL argument");
+    if (!aligned8(a) || !aligned8(b) || !aligned8(out)) return fail(NB_ERR_ARG, "pointers must be 8-byte aligned");
+    Mesh m;
+    m.ex = mesh.ex; m.ey = mesh.ey; m.ez = mesh.ez; m.n = n;
+    m.E = (int64_t)mesh.ex * mesh.ey * mesh.ez;
+    m.npts = m.E * n * n * n;
+    m.NX = (int64_t)mesh.ex * (n - 1) + 1;
+    m.NY = (int64_t)mesh.ey * (n - 1) + 1;
+    m.NZ = (int64_t)mesh.ez * (n - 1) + 1;
+    return dot_c_noalloc(m, a, b, out, (cudaStream_t)cuda_stream);
+    NB_GUARD_END
+}
+
 nb_status nb_scatter_unique(nb_ctx *c, const double *g, double *loc) {
     NB_GUARD_BEGIN
     if (!c || !g || !loc) return fail(NB_ERR_ARG, "NULL argument");

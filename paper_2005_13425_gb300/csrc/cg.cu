@@ -19,6 +19,8 @@
 // captured as CUDA graphs; every kernel returns at once when `done` is set.
 #include <math.h>
 
+#include <mutex>
+
 #include "internal.cuh"
 #include "reduce.cuh"
 
@@ -374,6 +376,63 @@ nb_status cg_solve_fp64(nb_ctx *c, const double *f, double *x, double tol, int m
     if (h.status == (int)NB_ERR_BREAKDOWN) return fail(NB_ERR_BREAKDOWN, "CG breakdown: <Ap,p>_c <= 0 or not finite");
     if (tol > 0.0 && !(rel <= tol) && h.rho != 0.0)
         return fail(NB_ERR_NOT_CONVERGED, "CG did not reach the tolerance within maxit");
+    return NB_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free dot
+// Some callers cannot call cudaMalloc: code recording a CUDA graph (device
+// allocation is not a capturable stream operation), code running under a
+// memory manager that already owns the device memory, and code that must
+// not block (cudaMalloc may synchronise the device).  For them the weighted
+// dot product runs the same reduction kernel with its scratch -- one
+// partial sum per element plus the last-CTA ticket -- in a file-scope
+// device array instead of a context's allocation.  Every GPU that loads the
+// library holds this array (about 256 KB) until the process exits.
+constexpr int kNoAllocMaxElements = 32768;
+
+struct NoAllocScratch {
+    double partials[kNoAllocMaxElements];
+    CgScalars sc;   // only the ticket is used
+};
+
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+static std::mutex g_noalloc_mu;
+static NoAllocScratch *g_noalloc_ptr[256];
+
+// Device address of the scratch on the current device, looked up once per
+// device (host code cannot use the symbol itself as a device address).
+static nb_status noalloc_scratch(NoAllocScratch **out) {
+    int dev = 0;
+    NB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return fail(NB_ERR_STATE, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(allocation-free scratch)");
+        g_noalloc_ptr[dev] = (NoAllocScratch *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return NB_OK;
+}
+
+nb_status dot_c_noalloc(const Mesh &m, const double *a, const double *b, double *out,
+                        cudaStream_t stream) {
+    if (m.E > kNoAllocMaxElements)
+        return fail(NB_ERR_ARG, "the allocation-free dot product supports at most 32768 elements");
+    NoAllocScratch *s = nullptr;
+    nb_status st = noalloc_scratch(&s);
+    if (st != NB_OK) return st;
+    // the ticket must start at zero; the partials are all overwritten
+    NB_CUDA(cudaMemsetAsync(&s->sc.ticket, 0, sizeof(unsigned int), stream));
+    const int grid = (int)m.E;   // one CTA, hence one partial slot, per element
+#define CALL(NN)                                                                                   \
+    dot_kernel<NN, 0><<<grid, kRedThreads, 0, stream>>>(a, b, nullptr, nullptr, m, s->partials,    \
+                                                       &s->sc, out, nullptr)
+    NB_DISPATCH_N(m.n, CALL)
+#undef CALL
+    NB_LAUNCH_CHECK("dot_kernel (allocation-free)");
     return NB_OK;
 }
 

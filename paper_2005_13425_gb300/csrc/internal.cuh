@@ -147,6 +147,8 @@ nb_status launch_box_geometry(nb_ctx *c, double amp, const double *s, int *bad_d
 nb_status launch_box_coords(nb_ctx *c, double *xyz);
 // reductions + CG (cg.cu)
 nb_status dot_c(nb_ctx *c, const double *a, const double *b, double *out_host);
+nb_status dot_c_noalloc(const Mesh &m, const double *a, const double *b, double *out,
+                        cudaStream_t stream);
 nb_status cg_solve_fp64(nb_ctx *c, const double *f, double *x, double tol, int maxit,
                         int *iters, double *relres);
 nb_status cg_solve_mixed(nb_ctx *c, const double *f, double *x, double tol, int maxit,

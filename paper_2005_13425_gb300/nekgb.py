@@ -67,6 +67,7 @@ _SIGS = {
     "nb_cg_solve_host": [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _ip, _dp],
     "nb_cg_history": [_vp, _vp, ctypes.c_int, _ip],
     "nb_dot_c": [_vp, _vp, _vp, _dp],
+    "nb_dot_c_noalloc": [nb_box, ctypes.c_int, _vp, _vp, _vp, _vp],
     "nb_scatter_unique": [_vp, _vp, _vp],
     "nb_tables": [_vp, _vp, _vp, _vp],
     "nb_get_operator": [_vp, _vp, _vp],
@@ -238,6 +239,14 @@ def nb_dot_c(ctx, a, b) -> float:
     _check(load().nb_dot_c(ctx, _ptr(a, "torch.float64"), _ptr(b, "torch.float64"),
                            ctypes.byref(out)), "nb_dot_c")
     return out.value
+
+
+def nb_dot_c_noalloc(mesh, n, a, b, out, stream=None):
+    """<a,b>_c into the 1-double device buffer `out`, with no context and no
+    allocation (asynchronous on `stream`)."""
+    _check(load().nb_dot_c_noalloc(nb_box(*mesh), int(n), _ptr(a, "torch.float64"),
+                                   _ptr(b, "torch.float64"), _ptr(out, "torch.float64"),
+                                   _stream_handle(stream)), "nb_dot_c_noalloc")
 
 
 def nb_scatter_unique(ctx, g, local):
