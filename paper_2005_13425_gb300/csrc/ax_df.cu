@@ -37,6 +37,28 @@ struct DfMat {
     float l[N * N];
 };
 
+// Even-odd form of a centro-antisymmetric matrix M (M(N-1-m, N-1-l) =
+// -M(m,l), which holds for the GLL derivative matrix and its transpose).
+// With H = N/2, xs_l = x_l + x_{N-1-l}, xd_l = x_l - x_{N-1-l} (l < H):
+//   y_m       = P_m + Q_m,   y_{N-1-m} = P_m - Q_m   (m < H)
+//   P_m = sum_{l<H} a(m,l) xd_l,            a(m,l) = (M(m,l) + M(N-1-m,l))/2
+//   Q_m = sum_{l<H} b(m,l) xs_l + b(m,H) x_H, b(m,l) = (M(m,l) - M(N-1-m,l))/2
+// and for odd N the middle output y_H = sum_{l<H} M(H,l) xd_l + M(H,H) x_H.
+// This halves the products of a line (Solomonoff's even-odd decomposition).
+template <int N>
+struct EoMat {
+    static constexpr int H = N / 2;
+    float ah[H * H], al[H * H];
+    float bh[H * (H + 1)], bl[H * (H + 1)];
+    float ch[H + 1], cl[H + 1];
+};
+
+template <int N>
+struct DfEo {
+    EoMat<N> fwd;   // M = D
+    EoMat<N> bwd;   // M = D^T
+};
+
 struct AxDfArgs {
     const double *u;      // MODE 0 input
     double *w;            // output (FP64, local storage)
@@ -77,9 +99,83 @@ __device__ __forceinline__ int line_of(int task, int &stride) {
     return a0 + N * a1;
 }
 
-template <int N, int MODE>
+// out(base + m*stride) = sum_l M(m,l) in(base + l*stride), M = D or D^T,
+// n compensated dot products of n terms.
+template <int N, bool TR>
+__device__ __forceinline__ void line_plain(const float2 *in, float2 *out, int base, int stride,
+                                           const DfMat<N> &D) {
+    float xh[N], xl[N];
+#pragma unroll
+    for (int l = 0; l < N; l++) {
+        const float2 v = in[base + l * stride];
+        xh[l] = v.x;
+        xl[l] = v.y;
+    }
+#pragma unroll
+    for (int m = 0; m < N; m++) {
+        const int i0 = TR ? m : m * N;
+        dfa::Acc acc = dfa::first(D.h[i0], D.l[i0], xh[0], xl[0]);
+#pragma unroll
+        for (int l = 1; l < N; l++) {
+            const int il = TR ? l * N + m : m * N + l;
+            dfa::fma(acc, D.h[il], D.l[il], xh[l], xl[l]);
+        }
+        out[base + m * stride] = dfa::norm(acc);
+    }
+}
+
+// The same line product in even-odd form (see EoMat): pair sums and
+// differences, then 2 dot products of N/2 terms per output pair.
+template <int N>
+__device__ __forceinline__ void line_eo(const float2 *in, float2 *out, int base, int stride,
+                                        const EoMat<N> &M) {
+    constexpr int H = N / 2;
+    float sh[H], sl[H], dh[H], dl[H];
+#pragma unroll
+    for (int l = 0; l < H; l++) {
+        const float2 a = in[base + l * stride], b = in[base + (N - 1 - l) * stride];
+        const float2 s = dfa::add(a, b);
+        const float2 d = dfa::add(a, make_float2(-b.x, -b.y));
+        sh[l] = s.x; sl[l] = s.y;
+        dh[l] = d.x; dl[l] = d.y;
+    }
+    float ch = 0.f, cl = 0.f;
+    if (N & 1) {
+        const float2 c = in[base + H * stride];
+        ch = c.x;
+        cl = c.y;
+    }
+#pragma unroll
+    for (int m = 0; m < H; m++) {
+        dfa::Acc P = dfa::first(M.ah[m * H], M.al[m * H], dh[0], dl[0]);
+#pragma unroll
+        for (int l = 1; l < H; l++) dfa::fma(P, M.ah[m * H + l], M.al[m * H + l], dh[l], dl[l]);
+        dfa::Acc Q = dfa::first(M.bh[m * (H + 1)], M.bl[m * (H + 1)], sh[0], sl[0]);
+#pragma unroll
+        for (int l = 1; l < H; l++) dfa::fma(Q, M.bh[m * (H + 1) + l], M.bl[m * (H + 1) + l], sh[l], sl[l]);
+        if (N & 1) dfa::fma(Q, M.bh[m * (H + 1) + H], M.bl[m * (H + 1) + H], ch, cl);
+        out[base + m * stride] = dfa::add_acc(P, Q, 1.f);
+        out[base + (N - 1 - m) * stride] = dfa::add_acc(P, Q, -1.f);
+    }
+    if (N & 1) {
+        dfa::Acc Y = dfa::first(M.ch[0], M.cl[0], dh[0], dl[0]);
+#pragma unroll
+        for (int l = 1; l < H; l++) dfa::fma(Y, M.ch[l], M.cl[l], dh[l], dl[l]);
+        dfa::fma(Y, M.ch[H], M.cl[H], ch, cl);
+        out[base + H * stride] = dfa::norm(Y);
+    }
+}
+
+template <int N, bool EO>
+struct DfConsts;
+template <int N>
+struct DfConsts<N, false> { using type = DfMat<N>; };
+template <int N>
+struct DfConsts<N, true> { using type = DfEo<N>; };
+
+template <int N, int MODE, bool EO>
 __global__ void __launch_bounds__(ax_df_threads(N))
-ax_df_kernel(AxDfArgs a, const __grid_constant__ DfMat<N> D) {
+ax_df_kernel(AxDfArgs a, const __grid_constant__ typename DfConsts<N, EO>::type D) {
     constexpr int N2 = N * N, N3 = N * N * N;
     constexpr int T = ax_df_threads(N);
     extern __shared__ float2 sm[];
@@ -139,20 +235,10 @@ ax_df_kernel(AxDfArgs a, const __grid_constant__ DfMat<N> D) {
             int stride;
             const int base = line_of<N>(task, stride);
             float2 *Wd = task < N2 ? W0 : (task < 2 * N2 ? W1 : W2);
-            float xh[N], xl[N];
-#pragma unroll
-            for (int l = 0; l < N; l++) {
-                const float2 v = U[base + l * stride];
-                xh[l] = v.x;
-                xl[l] = v.y;
-            }
-#pragma unroll
-            for (int m = 0; m < N; m++) {
-                dfa::Acc acc = dfa::first(D.h[m * N], D.l[m * N], xh[0], xl[0]);
-#pragma unroll
-                for (int l = 1; l < N; l++) dfa::fma(acc, D.h[m * N + l], D.l[m * N + l], xh[l], xl[l]);
-                Wd[base + m * stride] = dfa::norm(acc);
-            }
+            if constexpr (EO)
+                line_eo<N>(U, Wd, base, stride, D.fwd);
+            else
+                line_plain<N, false>(U, Wd, base, stride, D);
         }
         __syncthreads();
 
@@ -183,20 +269,10 @@ ax_df_kernel(AxDfArgs a, const __grid_constant__ DfMat<N> D) {
             const int base = line_of<N>(task, stride);
             const float2 *Ud = task < N2 ? W0 : (task < 2 * N2 ? W1 : W2);
             float2 *Pd = task < N2 ? U : (task < 2 * N2 ? P1 : P2);
-            float xh[N], xl[N];
-#pragma unroll
-            for (int l = 0; l < N; l++) {
-                const float2 v = Ud[base + l * stride];
-                xh[l] = v.x;
-                xl[l] = v.y;
-            }
-#pragma unroll
-            for (int m = 0; m < N; m++) {
-                dfa::Acc acc = dfa::first(D.h[m], D.l[m], xh[0], xl[0]);
-#pragma unroll
-                for (int l = 1; l < N; l++) dfa::fma(acc, D.h[l * N + m], D.l[l * N + m], xh[l], xl[l]);
-                Pd[base + m * stride] = dfa::norm(acc);
-            }
+            if constexpr (EO)
+                line_eo<N>(Ud, Pd, base, stride, D.bwd);
+            else
+                line_plain<N, true>(Ud, Pd, base, stride, D);
         }
         __syncthreads();
 
@@ -270,24 +346,59 @@ nb_status prepare_df(nb_ctx *c) {
     if (e != cudaSuccess) return cuda_fail(e, "split gxyz");
     gexp = gexp < 1 ? 1 : (gexp > 2046 ? 2046 : gexp);
     c->gxyz_exp = gexp;
+    c->d_eo = centro_antisymmetric(c->D_host, c->m.n);
     return NB_OK;
 }
 
 bool df_supported(int n) { return n >= 2 && n <= kMaxN; }
 
+// Even-odd constants of M (M = D, or D^T when tr) from the FP64 matrix.
 template <int N>
-static nb_status launch_df_n(nb_ctx *c, const double *u, double *w, int mode) {
+static void eo_consts(const double *Dm, bool tr, EoMat<N> &E) {
+    constexpr int H = N / 2;
+    auto M = [&](int m, int l) { return tr ? Dm[l * N + m] : Dm[m * N + l]; };
+    auto put = [](double v, float &h, float &l) {
+        h = (float)v;
+        l = (float)(v - (double)h);
+    };
+    for (int m = 0; m < H; m++) {
+        for (int l = 0; l < H; l++) put(0.5 * (M(m, l) + M(N - 1 - m, l)), E.ah[m * H + l], E.al[m * H + l]);
+        for (int l = 0; l <= H; l++) {
+            const double v = l < H ? 0.5 * (M(m, l) - M(N - 1 - m, l)) : ((N & 1) ? M(m, H) : 0.0);
+            put(v, E.bh[m * (H + 1) + l], E.bl[m * (H + 1) + l]);
+        }
+    }
+    for (int l = 0; l <= H; l++) put((N & 1) ? M(H, l) : 0.0, E.ch[l], E.cl[l]);
+}
+
+// True when D(i,l) = -D(n-1-i, n-1-l) to rounding (GLL derivative matrices).
+bool centro_antisymmetric(const double *D, int n) {
+    double mx = 0.0, asym = 0.0;
+    for (int q = 0; q < n * n; q++) mx = fmax(mx, fabs(D[q]));
+    for (int i = 0; i < n; i++)
+        for (int l = 0; l < n; l++)
+            asym = fmax(asym, fabs(D[i * n + l] + D[(n - 1 - i) * n + (n - 1 - l)]));
+    return asym <= 1e-14 * mx;
+}
+
+template <int N, bool EO>
+static nb_status launch_df_nv(nb_ctx *c, const double *u, double *w, int mode) {
     constexpr int T = ax_df_threads(N);
     const size_t smem = sizeof(float2) * 6 * N * N * N;
     static bool configured[2] = {false, false};
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    DfMat<N> D;
-    for (int q = 0; q < N * N; q++) {
-        const float h = (float)c->D_host[q];
-        D.h[q] = h;
-        D.l[q] = (float)(c->D_host[q] - (double)h);
+    typename DfConsts<N, EO>::type D;
+    if constexpr (EO) {
+        eo_consts<N>(c->D_host, false, D.fwd);
+        eo_consts<N>(c->D_host, true, D.bwd);
+    } else {
+        for (int q = 0; q < N * N; q++) {
+            const float h = (float)c->D_host[q];
+            D.h[q] = h;
+            D.l[q] = (float)(c->D_host[q] - (double)h);
+        }
     }
     AxDfArgs args{};
     args.g = c->d_gxyz_df;
@@ -306,7 +417,7 @@ static nb_status launch_df_n(nb_ctx *c, const double *u, double *w, int mode) {
         args.fuse = c->fused_cg ? 1 : 0;
     }
     args.m = c->m;
-    auto kern = mode == 0 ? ax_df_kernel<N, 0> : ax_df_kernel<N, 1>;
+    auto kern = mode == 0 ? ax_df_kernel<N, 0, EO> : ax_df_kernel<N, 1, EO>;
     if (!configured[mode]) {
         NB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured[mode] = true;
@@ -320,6 +431,11 @@ static nb_status launch_df_n(nb_ctx *c, const double *u, double *w, int mode) {
     kern<<<grid, T, smem, c->stream>>>(args, D);
     NB_LAUNCH_CHECK("ax_df_kernel");
     return NB_OK;
+}
+
+template <int N>
+static nb_status launch_df_n(nb_ctx *c, const double *u, double *w, int mode) {
+    return c->d_eo ? launch_df_nv<N, true>(c, u, w, mode) : launch_df_nv<N, false>(c, u, w, mode);
 }
 
 nb_status launch_ax_df(nb_ctx *c, const double *u, double *w, int mode) {

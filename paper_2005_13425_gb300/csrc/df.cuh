@@ -68,6 +68,17 @@ __device__ __forceinline__ float2 add(float2 a, float2 b) {
     return make_float2(h, l);
 }
 
+// (P.s + P.c) + sgn*(Q.s + Q.c) as a normalised pair (sgn = +1 or -1;
+// TwoSum on the leading parts, the compensations added after).
+__device__ __forceinline__ float2 add_acc(const Acc &P, const Acc &Q, float sgn) {
+    float s, e;
+    two_sum(P.s, sgn * Q.s, s, e);
+    e = __fadd_rn(e, __fadd_rn(P.c, sgn * Q.c));
+    const float h = __fadd_rn(s, e);
+    const float l = __fsub_rn(e, __fsub_rn(h, s));
+    return make_float2(h, l);
+}
+
 // Split a double into a normalised pair: h = fl32(x), l = fl32(x - h).
 // x - h is exact in FP64, so h + l carries 48 bits of x.
 __device__ __forceinline__ float2 split(double x) {

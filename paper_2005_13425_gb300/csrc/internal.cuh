@@ -82,6 +82,7 @@ struct nb_ctx {
     float2 *d_gxyz_df = nullptr;  // [E][6][n^3] (hi,lo) pairs for double-float ax
     float *d_gxyz32 = nullptr;  // [E][6][n^3] fp32 for the mixed inner solve
     int gxyz_exp = 1023;
+    bool d_eo = false;          // D is centro-antisymmetric: even-odd line products
     bool is_box = false;        // built by nb_setup_box (coordinates known)
     double box_amp = 0.0, box_s[3] = {0, 0, 0};        // biased exponent of max|gxyz| (pairs are scaled by 2^-(gxyz_exp-1023))
     // CG workspace
@@ -155,6 +156,7 @@ nb_status cg_solve_mixed(nb_ctx *c, const double *f, double *x, double tol, int 
                          int *iters, double *relres);
 nb_status ensure_cg_workspace(nb_ctx *c);
 nb_status prepare_df(nb_ctx *c);   // double-float copies of D and gxyz
+bool centro_antisymmetric(const double *D, int n);
 nb_status prepare_fp32(nb_ctx *c); // fp32 copy of gxyz for the mixed solve
 
 // ---------------------------------------------------------------- device helpers

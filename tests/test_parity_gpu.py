@@ -104,6 +104,23 @@ def test_ax_double_float_scale_invariance(nek, oracle, scale_u, scale_g):
     assert rel_err(got[1], want[1]) <= 1e-11
 
 
+@pytest.mark.parametrize("n", [5, 10])
+def test_ax_general_derivative_matrix(nek, oracle, n):
+    """A D without the GLL centro-antisymmetry takes the plain line
+    products (the even-odd form needs D(i,l) = -D(n-1-i, n-1-l))."""
+    dims = (3, 2, 2)
+    P = oracle_problem(oracle, dims, n, seed=9)
+    D = np.random.default_rng(n).uniform(-5, 5, (n, n))
+    u = inputs.local_field(P["E"], n, seed=4)
+    want = oracle.ax_e(D, P["gxyz"], u)
+    with Ctx(nek, dims, n, D, P["gxyz"]) as ctx:
+        for variant in (0, 1):
+            nek.nb_set_ax_variant(ctx, variant)
+            w = torch.empty(P["E"], n ** 3, dtype=torch.float64, device="cuda")
+            nek.nb_ax(ctx, dev(u), w)
+            assert rel_err(host(w), want) <= AX_TOL, variant
+
+
 def test_ax_ragged_many_elements(nek, oracle):
     """More elements than the grid holds at once, with a ragged last wave."""
     dims, n = (13, 11, 7), 6
