@@ -238,6 +238,75 @@ nb_status nb_solve_stats(const nb_ctx *ctx, int *iters, int *outer);
 nb_status nb_set_ax_variant(nb_ctx *ctx, int variant);
 
 /* --------------------------------------------------------------------- */
+/* Batched and served solves (the paper's small-problem limit, Sec. VI.B  */
+/* and VII: many small box problems share the GPU)                        */
+/* --------------------------------------------------------------------- */
+
+typedef struct nb_engine nb_engine;  /* opaque; owns a device arena */
+
+/* One solve request: the synthetic box problem of nb_setup_box (mesh, n,
+ * perturbation amp * s[d]) with right-hand side f, solved by FP64-accurate
+ * CG from x0 = 0 to relative residual tol (tol <= 0: exactly maxit
+ * iterations). */
+typedef struct {
+    nb_box mesh;
+    int n;
+    double amp;
+    double s[3];
+    double tol;
+    int maxit;
+} nb_request;
+
+/* Create an engine with a device arena of arena_bytes (>= 1 MiB) on
+ * cuda_stream.  Every admitted request lives in the arena. */
+nb_status nb_engine_create(nb_engine **out, size_t arena_bytes, void *cuda_stream);
+nb_status nb_engine_destroy(nb_engine *eng);
+
+/* Bytes of arena a request of this mesh and n needs (gxyz pairs, four CG
+ * vectors and reduction partials), the admission criterion. */
+nb_status nb_engine_footprint(nb_box mesh, int n, size_t *bytes);
+
+/* Admit a request: builds its geometry in the arena, copies f (device,
+ * E*n^3 doubles, local storage; continuous and masked) and starts its solve.
+ * *id_out receives the request id.  NB_ERR_OOM when the footprint does not
+ * fit in the free arena (or all 1024 request slots are in use): the caller
+ * retries after retiring finished requests.  The first request of a given n
+ * runs the autotuner (a few ms) unless NEKGB_TUNE_CACHE names a file that
+ * already holds the choice.  Blocks until the request is set up. */
+nb_status nb_engine_submit(nb_engine *eng, const nb_request *req, const double *f_dev,
+                           int *id_out);
+
+/* As nb_engine_submit with the right-hand side given per unique node:
+ * fu_dev (device, NX*NY*NZ doubles, x fastest) is copied to every local copy
+ * and zeroed on the faces of the box. */
+nb_status nb_engine_submit_unique(nb_engine *eng, const nb_request *req, const double *fu_dev,
+                                  int *id_out);
+
+/* Advance every active request by `iters` CG iterations (rounded up to a
+ * multiple of 8): per iteration, one launch per kernel and per distinct n
+ * covers all active requests of that n; the iterations are replayed from a
+ * captured CUDA graph.  Finished requests are skipped.  Blocks until done. */
+nb_status nb_engine_step(nb_engine *eng, int iters);
+
+/* State of a request after the last step: *done = 1 once it converged, hit
+ * maxit or broke down; iterations, relative residual sqrt(<r,r>_c/<f,f>_c)
+ * and the solve status (NB_OK, NB_ERR_NOT_CONVERGED, NB_ERR_BREAKDOWN). */
+nb_status nb_engine_poll(nb_engine *eng, int id, int *done, int *iters, double *relres,
+                         int *status);
+
+/* Copy the request's solution to x_dev (device, E*n^3 doubles; NULL to
+ * drop it) and free its slot and arena space.  Blocks until done. */
+nb_status nb_engine_retire(nb_engine *eng, int id, double *x_dev);
+
+/* Arena bytes in use, arena capacity and active requests. */
+nb_status nb_engine_stats(const nb_engine *eng, size_t *used, size_t *capacity, int *active);
+
+/* The autotuner's choice for n: line tasks per thread and elements per
+ * tile of the CG head kernel (0 if n has not been used yet). */
+nb_status nb_engine_tuning(const nb_engine *eng, int n, int *lines_per_thread,
+                           int *elems_per_tile);
+
+/* --------------------------------------------------------------------- */
 /* Kernel timing (CUDA events recorded on the context's stream)           */
 /* --------------------------------------------------------------------- */
 

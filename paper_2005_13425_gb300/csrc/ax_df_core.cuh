@@ -1,0 +1,307 @@
+// Core of the double-float ax_e (Listing 1, arXiv 2005.13425 Sec. III) shared
+// by the single-problem kernel (ax_df.cu) and the batched engine
+// (engine.cu): derivative-matrix constants, the line products (plain and
+// even-odd) and the per-element operator df_element().  See ax_df.cu for
+// the arithmetic and thread layout.
+#pragma once
+
+#include "df.cuh"
+#include "internal.cuh"
+#include "reduce.cuh"
+
+namespace nekgb {
+
+template <int N>
+struct DfMat {
+    float h[N * N];   // h[m*N + l] + l_[m*N + l] = D(m, l)
+    float l[N * N];
+};
+
+// Even-odd form of a centro-antisymmetric matrix M (M(N-1-m, N-1-l) =
+// -M(m,l), which holds for the GLL derivative matrix and its transpose).
+// With H = N/2, xs_l = x_l + x_{N-1-l}, xd_l = x_l - x_{N-1-l} (l < H):
+//   y_m       = P_m + Q_m,   y_{N-1-m} = P_m - Q_m   (m < H)
+//   P_m = sum_{l<H} a(m,l) xd_l,            a(m,l) = (M(m,l) + M(N-1-m,l))/2
+//   Q_m = sum_{l<H} b(m,l) xs_l + b(m,H) x_H, b(m,l) = (M(m,l) - M(N-1-m,l))/2
+// and for odd N the middle output y_H = sum_{l<H} M(H,l) xd_l + M(H,H) x_H.
+// This halves the products of a line (Solomonoff's even-odd decomposition).
+template <int N>
+struct EoMat {
+    static constexpr int H = N / 2;
+    float ah[H * H], al[H * H];
+    float bh[H * (H + 1)], bl[H * (H + 1)];
+    float ch[H + 1], cl[H + 1];
+};
+
+template <int N>
+struct DfEo {
+    EoMat<N> fwd;   // M = D
+    EoMat<N> bwd;   // M = D^T
+};
+
+
+// One line task per thread up to n = 12; two per thread above, so that the
+// n-long line held in registers does not spill at n = 16.
+__host__ __device__ constexpr int ax_df_threads(int n) {
+    return n <= 12 ? ((3 * n * n + 31) / 32) * 32 : ((3 * n * n + 1) / 2 + 31) / 32 * 32;
+}
+
+// Threads of a CTA that gives each thread `lpt` line tasks (lpt >= 1).
+__host__ __device__ constexpr int df_threads_lpt(int n, int lpt) {
+    return ((3 * n * n + lpt - 1) / lpt + 31) / 32 * 32;
+}
+
+// Line task -> (first point, stride) of the line and the direction.
+template <int N>
+__device__ __forceinline__ int line_of(int task, int &stride) {
+    constexpr int N2 = N * N;
+    const int d = task / N2;
+    const int c = task - d * N2;
+    const int a0 = c % N, a1 = c / N;
+    if (d == 0) {        // along r: line (j = a0, k = a1)
+        stride = 1;
+        return N * (a0 + N * a1);
+    }
+    if (d == 1) {        // along s: line (i = a0, k = a1)
+        stride = N;
+        return a0 + N2 * a1;
+    }
+    stride = N2;         // along t: line (i = a0, j = a1)
+    return a0 + N * a1;
+}
+
+// out(base + m*stride) = sum_l M(m,l) in(base + l*stride), M = D or D^T,
+// n compensated dot products of n terms.
+template <int N, bool TR>
+__device__ __forceinline__ void line_plain(const float2 *in, float2 *out, int base, int stride,
+                                           const DfMat<N> &D) {
+    float xh[N], xl[N];
+#pragma unroll
+    for (int l = 0; l < N; l++) {
+        const float2 v = in[base + l * stride];
+        xh[l] = v.x;
+        xl[l] = v.y;
+    }
+#pragma unroll
+    for (int m = 0; m < N; m++) {
+        const int i0 = TR ? m : m * N;
+        dfa::Acc acc = dfa::first(D.h[i0], D.l[i0], xh[0], xl[0]);
+#pragma unroll
+        for (int l = 1; l < N; l++) {
+            const int il = TR ? l * N + m : m * N + l;
+            dfa::fma(acc, D.h[il], D.l[il], xh[l], xl[l]);
+        }
+        out[base + m * stride] = dfa::norm(acc);
+    }
+}
+
+// The same line product in even-odd form (see EoMat): pair sums and
+// differences, then 2 dot products of N/2 terms per output pair.
+template <int N>
+__device__ __forceinline__ void line_eo(const float2 *in, float2 *out, int base, int stride,
+                                        const EoMat<N> &M) {
+    constexpr int H = N / 2;
+    float sh[H], sl[H], dh[H], dl[H];
+#pragma unroll
+    for (int l = 0; l < H; l++) {
+        const float2 a = in[base + l * stride], b = in[base + (N - 1 - l) * stride];
+        const float2 s = dfa::add(a, b);
+        const float2 d = dfa::add(a, make_float2(-b.x, -b.y));
+        sh[l] = s.x; sl[l] = s.y;
+        dh[l] = d.x; dl[l] = d.y;
+    }
+    float ch = 0.f, cl = 0.f;
+    if (N & 1) {
+        const float2 c = in[base + H * stride];
+        ch = c.x;
+        cl = c.y;
+    }
+#pragma unroll
+    for (int m = 0; m < H; m++) {
+        dfa::Acc P = dfa::first(M.ah[m * H], M.al[m * H], dh[0], dl[0]);
+#pragma unroll
+        for (int l = 1; l < H; l++) dfa::fma(P, M.ah[m * H + l], M.al[m * H + l], dh[l], dl[l]);
+        dfa::Acc Q = dfa::first(M.bh[m * (H + 1)], M.bl[m * (H + 1)], sh[0], sl[0]);
+#pragma unroll
+        for (int l = 1; l < H; l++) dfa::fma(Q, M.bh[m * (H + 1) + l], M.bl[m * (H + 1) + l], sh[l], sl[l]);
+        if (N & 1) dfa::fma(Q, M.bh[m * (H + 1) + H], M.bl[m * (H + 1) + H], ch, cl);
+        out[base + m * stride] = dfa::add_acc(P, Q, 1.f);
+        out[base + (N - 1 - m) * stride] = dfa::add_acc(P, Q, -1.f);
+    }
+    if (N & 1) {
+        dfa::Acc Y = dfa::first(M.ch[0], M.cl[0], dh[0], dl[0]);
+#pragma unroll
+        for (int l = 1; l < H; l++) dfa::fma(Y, M.ch[l], M.cl[l], dh[l], dl[l]);
+        dfa::fma(Y, M.ch[H], M.cl[H], ch, cl);
+        out[base + H * stride] = dfa::norm(Y);
+    }
+}
+
+template <int N, bool EO>
+struct DfConsts;
+template <int N>
+struct DfConsts<N, false> { using type = DfMat<N>; };
+template <int N>
+struct DfConsts<N, true> { using type = DfEo<N>; };
+
+
+// Per-element arguments of df_element (pointers already offset to the element).
+struct DfElemIO {
+    const double *u;    // MODE 0: input
+    const double *r;    // MODE 1: residual
+    double *p;          // MODE 1: search direction (updated in place)
+    double *x;          // MODE 1: iterate (owed update applied when xa != 0)
+    double *w;          // output
+    const float2 *g;    // gxyz pairs [6][n^3] of the element, scaled by 2^-(gexp-1023)
+};
+
+// One element of ax_e in double-float arithmetic, executed by the whole CTA
+// (every thread must call it; it contains barriers).  sm holds 6 n^3 pairs,
+// s_emax is a shared int that must be 0 on entry (left 0 on exit).
+// MODE 1 is the CG head: x += xa p, p = r + beta p, w = ax_e(p); with fuse,
+// box-face points of w are zeroed and the element-interior <w,p> is added
+// to dot.  (ex, ey, ez) is the element's position in the box m.
+template <int N, int MODE, bool EO, int T = ax_df_threads(N)>
+__device__ __forceinline__ void df_element(const DfElemIO &io, double beta, double xa, bool fuse,
+                                           int gexp, const Mesh &m, int ex, int ey, int ez,
+                                           const typename DfConsts<N, EO>::type &D, float2 *sm,
+                                           int *s_emax, double &dot) {
+    constexpr int N2 = N * N, N3 = N * N * N;
+    float2 *U = sm;            // input pairs; later the r-partial of w
+    float2 *W0 = sm + N3;      // wr -> ur
+    float2 *W1 = sm + 2 * N3;  // ws -> us
+    float2 *W2 = sm + 3 * N3;  // wt -> ut
+    float2 *P1 = sm + 4 * N3;  // s-partial of w
+    float2 *P2 = sm + 5 * N3;  // t-partial of w
+    double *raw = reinterpret_cast<double *>(U);
+    const int t = threadIdx.x;
+    // ---- stage the element (raw FP64 first, to find its scale)
+    int emax = 0;
+    for (int q = t; q < N3; q += T) {
+        double v;
+        if (MODE == 1) {
+            // x += alpha p of the previous iteration, then p = r + beta p
+            const double pold = io.p[q];
+            if (xa != 0.0) io.x[q] = fma(xa, pold, io.x[q]);
+            v = fma(beta, pold, io.r[q]);
+            io.p[q] = v;
+        } else {
+            v = __ldg(io.u + q);
+        }
+        raw[q] = v;
+        const int exb = (int)((__double_as_longlong(v) >> 52) & 0x7ff);
+        emax = exb > emax ? exb : emax;
+    }
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    if ((t & 31) == 0) atomicMax(s_emax, emax);
+    __syncthreads();
+    int eu = *s_emax;
+    eu = eu < 1 ? 1 : (eu > 2046 ? 2046 : eu);
+    // u is scaled by 2^(1023-eu) so the element's max is in [1,2); w is
+    // scaled back by 2^(eu-1023) and by the gxyz scale 2^(gexp-1023)
+    const int sh_in = 1023 - eu;
+    const int sh_out = (eu - 1023) + (gexp - 1023);
+    for (int q = t; q < N3; q += T) U[q] = dfa::split_scaled(raw[q], sh_in);  // own entries only
+    __syncthreads();
+
+    // ---- forward: wr, ws, wt along this thread's line
+    for (int task = t; task < 3 * N2; task += T) {
+        int stride;
+        const int base = line_of<N>(task, stride);
+        float2 *Wd = task < N2 ? W0 : (task < 2 * N2 ? W1 : W2);
+        if constexpr (EO)
+            line_eo<N>(U, Wd, base, stride, D.fwd);
+        else
+            line_plain<N, false>(U, Wd, base, stride, D);
+    }
+    __syncthreads();
+
+    // ---- geometric contraction, pointwise, in place
+    const float2 *g = io.g;
+    for (int q = t; q < N3; q += T) {
+        const float2 wr = W0[q], ws = W1[q], wt = W2[q];
+        const float2 g0 = g[q], g1 = g[N3 + q], g2 = g[2 * N3 + q];
+        const float2 g3 = g[3 * N3 + q], g4 = g[4 * N3 + q], g5 = g[5 * N3 + q];
+        dfa::Acc r = dfa::first(g0.x, g0.y, wr.x, wr.y);
+        dfa::fma(r, g1.x, g1.y, ws.x, ws.y);
+        dfa::fma(r, g2.x, g2.y, wt.x, wt.y);
+        dfa::Acc s = dfa::first(g1.x, g1.y, wr.x, wr.y);
+        dfa::fma(s, g3.x, g3.y, ws.x, ws.y);
+        dfa::fma(s, g4.x, g4.y, wt.x, wt.y);
+        dfa::Acc tt = dfa::first(g2.x, g2.y, wr.x, wr.y);
+        dfa::fma(tt, g4.x, g4.y, ws.x, ws.y);
+        dfa::fma(tt, g5.x, g5.y, wt.x, wt.y);
+        W0[q] = dfa::norm(r);
+        W1[q] = dfa::norm(s);
+        W2[q] = dfa::norm(tt);
+    }
+    __syncthreads();
+
+    // ---- backward: w_d(m) = sum_l dxtm1(m,l) u_d(l) = sum_l D(l,m) u_d(l)
+    for (int task = t; task < 3 * N2; task += T) {
+        int stride;
+        const int base = line_of<N>(task, stride);
+        const float2 *Ud = task < N2 ? W0 : (task < 2 * N2 ? W1 : W2);
+        float2 *Pd = task < N2 ? U : (task < 2 * N2 ? P1 : P2);
+        if constexpr (EO)
+            line_eo<N>(Ud, Pd, base, stride, D.bwd);
+        else
+            line_plain<N, true>(Ud, Pd, base, stride, D);
+    }
+    __syncthreads();
+
+    // ---- w = r-partial + s-partial + t-partial, scaled back, FP64 out
+    for (int q = t; q < N3; q += T) {
+        const float2 s = dfa::add(dfa::add(U[q], P1[q]), P2[q]);
+        double wv = dfa::join_scaled(s, sh_out);
+        if (MODE == 1 && fuse) {
+            // Dirichlet points are zeroed before dssum (their sum is then
+            // +0, as mask-after-dssum gives); element-interior points have
+            // multiplicity 1 and are final: <w,p> here.
+            const int i = q % N, j = (q / N) % N, k = q / N2;
+            if (on_box_face(i, j, k, ex, ey, ez, m))
+                wv = 0.0;
+            else if (i > 0 && i < N - 1 && j > 0 && j < N - 1 && k > 0 && k < N - 1)
+                dot = fma(wv, io.p[q], dot);
+        }
+        io.w[q] = wv;
+    }
+    if (t == 0) *s_emax = 0;
+    __syncthreads();
+}
+
+// Even-odd constants of M (M = D, or D^T when tr) from the FP64 matrix.
+template <int N>
+inline void eo_consts(const double *Dm, bool tr, EoMat<N> &E) {
+    constexpr int H = N / 2;
+    auto M = [&](int mm, int l) { return tr ? Dm[l * N + mm] : Dm[mm * N + l]; };
+    auto put = [](double v, float &h, float &l) {
+        h = (float)v;
+        l = (float)(v - (double)h);
+    };
+    for (int mm = 0; mm < H; mm++) {
+        for (int l = 0; l < H; l++) put(0.5 * (M(mm, l) + M(N - 1 - mm, l)), E.ah[mm * H + l], E.al[mm * H + l]);
+        for (int l = 0; l <= H; l++) {
+            const double v = l < H ? 0.5 * (M(mm, l) - M(N - 1 - mm, l)) : ((N & 1) ? M(mm, H) : 0.0);
+            put(v, E.bh[mm * (H + 1) + l], E.bl[mm * (H + 1) + l]);
+        }
+    }
+    for (int l = 0; l <= H; l++) put((N & 1) ? M(H, l) : 0.0, E.ch[l], E.cl[l]);
+}
+
+// Fill the kernel-parameter constants for D (plain pairs or even-odd form).
+template <int N, bool EO>
+inline void df_consts(const double *Dh, typename DfConsts<N, EO>::type &D) {
+    if constexpr (EO) {
+        eo_consts<N>(Dh, false, D.fwd);
+        eo_consts<N>(Dh, true, D.bwd);
+    } else {
+        for (int q = 0; q < N * N; q++) {
+            const float h = (float)Dh[q];
+            D.h[q] = h;
+            D.l[q] = (float)(Dh[q] - (double)h);
+        }
+    }
+}
+
+}  // namespace nekgb

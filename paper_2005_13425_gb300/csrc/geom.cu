@@ -79,6 +79,13 @@ nb_status host_dmat(int n, const double *x, double *D) {
     return NB_OK;
 }
 
+__device__ __forceinline__ void store_g(double *dst, double v) { *dst = v; }
+// pairs (hi, lo) for the double-float operator, unscaled
+__device__ __forceinline__ void store_g(float2 *dst, double v) {
+    const float h = __double2float_rn(v);
+    *dst = make_float2(h, __double2float_rn(v - (double)h));
+}
+
 struct GeomParams {
     double xi[kMaxN], w[kMaxN], D[kMaxN * kMaxN];
     double amp, s[3];
@@ -87,7 +94,8 @@ struct GeomParams {
 // One CTA per element (grid-stride).  Nodal coordinates are the affine box
 // position plus amp*s_d*sin(pi X) sin(pi Y) sin(pi Z); the Jacobian applies
 // D to the nodal coordinates along r, s and t (isoparametric mapping).
-__global__ void box_geometry_kernel(double *__restrict__ gxyz, Mesh m, GeomParams gp,
+template <typename OutT>
+__global__ void box_geometry_kernel(OutT *__restrict__ gxyz, Mesh m, GeomParams gp,
                                     int *__restrict__ bad) {
     const int n = m.n;
     const int64_t n3 = (int64_t)n * n * n;
@@ -147,8 +155,8 @@ __global__ void box_geometry_kernel(double *__restrict__ gxyz, Mesh m, GeomParam
                 const int b = bb[q], c = cc[q];
                 G[q] = (C[0][b] * C[0][c] + C[1][b] * C[1][c] + C[2][b] * C[2][c]) * sc;
             }
-            double *g = gxyz + e * 6 * n3 + p;
-            for (int q = 0; q < 6; q++) g[q * n3] = G[q];
+            OutT *g = gxyz + e * 6 * n3 + p;
+            for (int q = 0; q < 6; q++) store_g(g + q * n3, G[q]);
         }
     }
 }
@@ -201,8 +209,27 @@ nb_status launch_box_geometry(nb_ctx *c, double amp, const double *s, int *bad_d
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = (int)(c->m.E < (int64_t)sms * 8 ? c->m.E : (int64_t)sms * 8);
-    box_geometry_kernel<<<grid, 256, 0, c->stream>>>(c->d_gxyz, c->m, gp, bad_dev);
+    box_geometry_kernel<double><<<grid, 256, 0, c->stream>>>(c->d_gxyz, c->m, gp, bad_dev);
     NB_LAUNCH_CHECK("box_geometry_kernel");
+    return NB_OK;
+}
+
+// Geometric factors of a perturbed box as (hi, lo) float pairs (no scaling),
+// for problems of the batched engine; D is the context-free GLL matrix.
+nb_status launch_box_geometry_pairs(const Mesh &m, double amp, const double *s, const double *D,
+                                    float2 *out, int *bad_dev, cudaStream_t stream) {
+    GeomParams gp;
+    nb_status st = host_gll(m.n, gp.xi, gp.w);
+    if (st != NB_OK) return st;
+    for (int q = 0; q < m.n * m.n; q++) gp.D[q] = D[q];
+    gp.amp = amp;
+    gp.s[0] = s[0]; gp.s[1] = s[1]; gp.s[2] = s[2];
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)(m.E < (int64_t)sms * 8 ? m.E : (int64_t)sms * 8);
+    box_geometry_kernel<float2><<<grid, 256, 0, stream>>>(out, m, gp, bad_dev);
+    NB_LAUNCH_CHECK("box_geometry_kernel<pairs>");
     return NB_OK;
 }
 

@@ -146,6 +146,8 @@ nb_status host_gll(int n, double *xi, double *w);
 nb_status host_dmat(int n, const double *xi, double *D);
 nb_status launch_box_geometry(nb_ctx *c, double amp, const double *s, int *bad_dev);
 nb_status launch_box_coords(nb_ctx *c, double *xyz);
+nb_status launch_box_geometry_pairs(const Mesh &m, double amp, const double *s, const double *D,
+                                    float2 *out, int *bad_dev, cudaStream_t stream);
 // reductions + CG (cg.cu)
 nb_status dot_c(nb_ctx *c, const double *a, const double *b, double *out_host);
 nb_status dot_c_noalloc(const Mesh &m, const double *a, const double *b, double *out,

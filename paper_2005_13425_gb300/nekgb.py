@@ -47,6 +47,11 @@ class nb_info(ctypes.Structure):
                 ("ax_variant", ctypes.c_int), ("device_bytes", ctypes.c_size_t)]
 
 
+class nb_request(ctypes.Structure):
+    _fields_ = [("mesh", nb_box), ("n", ctypes.c_int), ("amp", ctypes.c_double),
+                ("s", ctypes.c_double * 3), ("tol", ctypes.c_double), ("maxit", ctypes.c_int)]
+
+
 _lib = None
 _lock = threading.Lock()
 _vp = ctypes.c_void_p
@@ -77,6 +82,16 @@ _SIGS = {
     "nb_dssum_f32": [_vp, _vp],
     "nb_set_mixed_params": [_vp, ctypes.c_double, ctypes.c_int],
     "nb_solve_stats": [_vp, _ip, _ip],
+    "nb_engine_create": [ctypes.POINTER(_vp), ctypes.c_size_t, _vp],
+    "nb_engine_destroy": [_vp],
+    "nb_engine_footprint": [nb_box, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
+    "nb_engine_submit": [_vp, ctypes.POINTER(nb_request), _vp, _ip],
+    "nb_engine_submit_unique": [_vp, ctypes.POINTER(nb_request), _vp, _ip],
+    "nb_engine_step": [_vp, ctypes.c_int],
+    "nb_engine_poll": [_vp, ctypes.c_int, _ip, _ip, _dp, _ip],
+    "nb_engine_retire": [_vp, ctypes.c_int, _vp],
+    "nb_engine_stats": [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t), _ip],
+    "nb_engine_tuning": [_vp, ctypes.c_int, _ip, _ip],
     "nb_timing_enable": [_vp, ctypes.c_int],
     "nb_timing_read": [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
 }
@@ -304,6 +319,73 @@ def nb_timing_read(ctx, kernel_id: int, reset: bool = False):
     _check(load().nb_timing_read(ctx, int(kernel_id), ctypes.byref(ms), ctypes.byref(cnt),
                                  1 if reset else 0), "nb_timing_read")
     return ms.value, cnt.value
+
+
+# ------------------------------------------------------------------ engine
+def nb_engine_create(arena_bytes: int, stream=None):
+    eng = _vp()
+    _check(load().nb_engine_create(ctypes.byref(eng), int(arena_bytes), _stream_handle(stream)),
+           "nb_engine_create")
+    return eng
+
+
+def nb_engine_destroy(eng):
+    _check(load().nb_engine_destroy(eng), "nb_engine_destroy")
+
+
+def nb_engine_footprint(mesh, n) -> int:
+    b = ctypes.c_size_t(0)
+    _check(load().nb_engine_footprint(nb_box(*mesh), int(n), ctypes.byref(b)), "nb_engine_footprint")
+    return b.value
+
+
+def nb_engine_submit(eng, mesh, n, amp, s, tol, maxit, f, allow=(NB_OK,)):
+    """Returns (status, id); id is -1 when the request was not admitted."""
+    req = nb_request(nb_box(*mesh), int(n), float(amp), (ctypes.c_double * 3)(*[float(v) for v in s]),
+                     float(tol), int(maxit))
+    rid = ctypes.c_int(-1)
+    st = load().nb_engine_submit(eng, ctypes.byref(req), _ptr(f, "torch.float64"), ctypes.byref(rid))
+    _check(st, "nb_engine_submit", allow)
+    return st, (rid.value if st == NB_OK else -1)
+
+
+def nb_engine_submit_unique(eng, mesh, n, amp, s, tol, maxit, fu, allow=(NB_OK,)):
+    """nb_engine_submit with f given per unique node (device, NX*NY*NZ)."""
+    req = nb_request(nb_box(*mesh), int(n), float(amp), (ctypes.c_double * 3)(*[float(v) for v in s]),
+                     float(tol), int(maxit))
+    rid = ctypes.c_int(-1)
+    st = load().nb_engine_submit_unique(eng, ctypes.byref(req), _ptr(fu, "torch.float64"), ctypes.byref(rid))
+    _check(st, "nb_engine_submit_unique", allow)
+    return st, (rid.value if st == NB_OK else -1)
+
+
+def nb_engine_step(eng, iters: int):
+    _check(load().nb_engine_step(eng, int(iters)), "nb_engine_step")
+
+
+def nb_engine_poll(eng, rid: int):
+    """(done, iterations, relres, status)."""
+    d, it, st = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    _check(load().nb_engine_poll(eng, int(rid), ctypes.byref(d), ctypes.byref(it), ctypes.byref(rr),
+                                 ctypes.byref(st)), "nb_engine_poll")
+    return bool(d.value), it.value, rr.value, st.value
+
+
+def nb_engine_retire(eng, rid: int, x=None):
+    _check(load().nb_engine_retire(eng, int(rid), _ptr(x, "torch.float64")), "nb_engine_retire")
+
+
+def nb_engine_stats(eng):
+    u, c, a = ctypes.c_size_t(0), ctypes.c_size_t(0), ctypes.c_int(0)
+    _check(load().nb_engine_stats(eng, ctypes.byref(u), ctypes.byref(c), ctypes.byref(a)), "nb_engine_stats")
+    return u.value, c.value, a.value
+
+
+def nb_engine_tuning(eng, n: int):
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().nb_engine_tuning(eng, int(n), ctypes.byref(a), ctypes.byref(b)), "nb_engine_tuning")
+    return a.value, b.value
 
 
 def nb_status_str(status: int) -> str:

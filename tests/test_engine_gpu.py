@@ -1,0 +1,131 @@
+"""Batched / served solves through the engine (nb_engine_*).
+
+* Each admitted problem converges: its returned x has an FP64 residual, in
+  the oracle's operator, within 2x the requested tolerance.
+* A problem's result is bit-identical whether it is solved alone or in a
+  mix of other problems (per-problem tiles and fixed-order reductions).
+* Admission is by arena footprint: too-large requests are refused with
+  NB_ERR_OOM until retired requests free space.
+"""
+import numpy as np
+import pytest
+
+from paper_2005_13425_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GIB = 1 << 30
+
+
+@pytest.fixture(scope="module")
+def nek(tmp_path_factory):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    os.environ.setdefault("NEKGB_TUNE_CACHE", str(tmp_path_factory.mktemp("tune") / "tune.txt"))
+    from paper_2005_13425_gb300 import build as b
+    b.build()
+    from paper_2005_13425_gb300 import nekgb
+    nekgb.load()
+    torch.cuda.set_stream(torch.cuda.Stream())
+    return nekgb
+
+
+def problem(oracle, dims, n, pid):
+    s = inputs.perturbation_coeffs(100 + pid)
+    P = oracle.box_problem(*dims, n, inputs.PERTURB_AMP, s)
+    f = oracle.apply_mask(P["mask"], oracle.scatter_unique(*dims, n, inputs.unique_field(*dims, n, seed=200 + pid)))
+    return P, s, f
+
+
+def run_engine(nek, items, arena=4 * GIB, iters_per_step=64, max_steps=400):
+    """items: list of (dims, n, s, f, tol, maxit).  Returns per-item (x, iters, relres, status)."""
+    stream = torch.cuda.current_stream()
+    eng = nek.nb_engine_create(arena, stream)
+    try:
+        ids = []
+        for dims, n, s, f, tol, maxit in items:
+            st, rid = nek.nb_engine_submit(eng, dims, n, inputs.PERTURB_AMP, s, tol, maxit,
+                                           torch.from_numpy(f).cuda())
+            ids.append(rid)
+        out = [None] * len(items)
+        for _ in range(max_steps):
+            nek.nb_engine_step(eng, iters_per_step)
+            for k, rid in enumerate(ids):
+                if out[k] is None:
+                    done, it, rr, st = nek.nb_engine_poll(eng, rid)
+                    if done:
+                        x = torch.empty(items[k][3].shape, dtype=torch.float64, device="cuda")
+                        nek.nb_engine_retire(eng, rid, x)
+                        stream.synchronize()
+                        out[k] = (x.cpu().numpy(), it, rr, st)
+            if all(o is not None for o in out):
+                break
+        return out
+    finally:
+        nek.nb_engine_destroy(eng)
+
+
+def true_relres(oracle, dims, n, P, f, x):
+    r = f - oracle.apply_A(*dims, n, P["D"], P["gxyz"], P["mask"], x)
+    return np.sqrt(oracle.dot_c(*dims, n, r, r) / oracle.dot_c(*dims, n, f, f))
+
+
+def test_engine_batch_converges_against_oracle(nek, oracle):
+    specs = [((2, 2, 2), 6), ((4, 2, 2), 8), ((2, 2, 1), 10), ((3, 2, 2), 6), ((2, 2, 2), 12)]
+    items, probs = [], []
+    for pid, (dims, n) in enumerate(specs):
+        P, s, f = problem(oracle, dims, n, pid)
+        probs.append((dims, n, P, f))
+        items.append((dims, n, s, f, 1e-10, 5000))
+    out = run_engine(nek, items)
+    for (dims, n, P, f), (x, it, rr, st) in zip(probs, out):
+        assert st == nek.NB_OK and rr <= 1e-10 and it > 0
+        assert true_relres(oracle, dims, n, P, f, x) <= 2e-10
+
+
+def test_engine_alone_equals_mix(nek, oracle):
+    target = ((3, 2, 2), 8)
+    P, s, f = problem(oracle, *target, 7)
+    item = (target[0], target[1], s, f, 1e-10, 5000)
+    alone = run_engine(nek, [item])[0]
+    others = []
+    for pid, (dims, n) in enumerate([((2, 2, 2), 6), ((4, 4, 2), 8), ((2, 1, 1), 10)]):
+        _, s2, f2 = problem(oracle, dims, n, 20 + pid)
+        others.append((dims, n, s2, f2, 1e-9, 3000))
+    mixed = run_engine(nek, others[:2] + [item] + others[2:])[2]
+    assert alone[1] == mixed[1] and alone[2] == mixed[2]
+    assert np.array_equal(alone[0], mixed[0])          # bit-identical
+
+
+def test_engine_fixed_iterations_match_single_solver(nek, oracle):
+    dims, n = (3, 3, 2), 6
+    P, s, f = problem(oracle, dims, n, 3)
+    x_eng, it, rr, st = run_engine(nek, [(dims, n, s, f, 0.0, 24)], iters_per_step=8)[0]
+    assert it == 24
+    x_ref, it_ref, rr_ref, _, _ = oracle.cg(*dims, n, P["D"], P["gxyz"], P["mask"], f, tol=0.0, maxit=24)
+    assert np.abs(x_eng - x_ref).max() <= 1e-8 * np.abs(x_ref).max()
+    assert abs(rr - rr_ref) <= 1e-8 * rr_ref
+
+
+def test_engine_admission_by_footprint(nek, oracle):
+    dims, n = (4, 4, 4), 8
+    need = nek.nb_engine_footprint(dims, n)
+    _, s, f = problem(oracle, dims, n, 5)
+    fd = torch.from_numpy(f).cuda()
+    eng = nek.nb_engine_create(int(need * 1.5) + (1 << 20), torch.cuda.current_stream())
+    try:
+        st1, a = nek.nb_engine_submit(eng, dims, n, 0.05, s, 1e-8, 100, fd)
+        st2, b = nek.nb_engine_submit(eng, dims, n, 0.05, s, 1e-8, 100, fd, allow=(nek.NB_OK, nek.NB_ERR_OOM))
+        assert st1 == nek.NB_OK and st2 == nek.NB_ERR_OOM and b == -1
+        used, cap, active = nek.nb_engine_stats(eng)
+        assert active == 1 and used >= need
+        nek.nb_engine_retire(eng, a)
+        st3, c = nek.nb_engine_submit(eng, dims, n, 0.05, s, 1e-8, 100, fd)
+        assert st3 == nek.NB_OK
+        lpt, te = nek.nb_engine_tuning(eng, n)
+        assert lpt in (1, 2) and te in (4, 8, 16)
+        nek.nb_engine_retire(eng, c)
+    finally:
+        nek.nb_engine_destroy(eng)
