@@ -431,6 +431,21 @@ def run_gpu(args, rank, world, local):
     }
     if not args.no_mixed:
         line["mixed_vs_fp64"] = [mixed_vs_fp64(nekgb, stream, nn) for nn in (8, 10)]
+    if not args.no_engine:
+        from paper_2005_13425_gb300 import workloads
+        batch = workloads.batch_list(256, seed=4)
+        line["batched"] = workloads.batched_run(nekgb, stream, batch, iters=100)
+        line["batched"]["config"] = ("256 box problems, E log-uniform in [64, 4096] rounded to box dims, "
+                                     "n from {6, 8, 10, 12}, FP64-accurate, 100 fixed CG iterations")
+        reqs = workloads.serving_requests(args.serve_requests, seed=5)
+        arena = 48 << 30
+        its = workloads.measure_iterations(nekgb, stream, reqs, arena)
+        cap = line["batched"]["gdofs"] * 1e9
+        line["serving"] = [workloads.serving_run(nekgb, stream, reqs, u, cap, its, arena)
+                           for u in (0.5, 0.95)]
+        for srv in line["serving"]:
+            srv["config"] = (f"{len(reqs)} requests, Poisson arrivals, E log-uniform in [64, 32768], "
+                             "n from {6, 8, 10, 12}, tol 1e-8 or 1e-10, FP64-accurate, 48 GiB arena")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     nekgb.nb_destroy(ctx)
@@ -448,6 +463,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-vs-FP64 solves")
+    ap.add_argument("--no-engine", action="store_true", help="skip the batched and served solves")
+    ap.add_argument("--serve-requests", type=int, default=32)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -76,6 +76,13 @@ def _load():
             lib.nbo_cg.argtypes = ([ctypes.c_int] * 4 + [_dp, _dp, _u8p, _dp, _dp,
                                    ctypes.c_double, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_int), _dp, _dp])
+            lib.nbo_diag_e.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+            lib.nbo_diag_e.restype = None
+            lib.nbo_jacobi_inverse.argtypes = [ctypes.c_int] * 4 + [_dp, _dp, _u8p, _dp]
+            lib.nbo_jacobi_inverse.restype = None
+            lib.nbo_pcg.argtypes = ([ctypes.c_int] * 4 + [_dp, _dp, _u8p, _dp, _dp, _dp,
+                                    ctypes.c_double, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int), _dp, _dp])
             _lib = lib
     return _lib
 
@@ -201,6 +208,39 @@ def cg(Ex, Ey, Ez, n, D, gxyz, msk, f, x0=None, tol=0.0, maxit=100):
                         _c(msk, np.uint8).ctypes.data_as(_u8p), _d(f), _d(x),
                         float(tol), int(maxit), ctypes.byref(iters),
                         ctypes.byref(relres), _d(hist))
+    return x, iters.value, relres.value, hist[: iters.value + 1].copy(), st
+
+
+def diag_e(D, gxyz):
+    """Diagonal of every element matrix of Listing 1, [E][n^3]."""
+    D = _c(D)
+    n = D.shape[0]
+    gxyz = _c(gxyz)
+    E = gxyz.size // (6 * n ** 3)
+    out = np.empty((E, n ** 3))
+    _load().nbo_diag_e(E, n, _d(D), _d(gxyz), _d(out))
+    return out
+
+
+def jacobi_inverse(Ex, Ey, Ez, n, D, gxyz, msk):
+    """1 / dssum(diag_e) at unmasked points, 0 at Dirichlet points."""
+    E = Ex * Ey * Ez
+    out = np.empty((E, n ** 3))
+    _load().nbo_jacobi_inverse(Ex, Ey, Ez, n, _d(_c(D)), _d(_c(gxyz)),
+                               _c(msk, np.uint8).ctypes.data_as(_u8p), _d(out))
+    return out
+
+
+def pcg(Ex, Ey, Ez, n, D, gxyz, msk, minv, f, x0=None, tol=0.0, maxit=100):
+    """Jacobi PCG.  Returns (x, iters, relres, rr_hist, status)."""
+    f = _c(f)
+    x = np.zeros_like(f) if x0 is None else _c(x0).copy()
+    hist = np.zeros(maxit + 1)
+    iters = ctypes.c_int(0)
+    relres = ctypes.c_double(0.0)
+    st = _load().nbo_pcg(Ex, Ey, Ez, n, _d(_c(D)), _d(_c(gxyz)),
+                         _c(msk, np.uint8).ctypes.data_as(_u8p), _d(_c(minv)), _d(f), _d(x),
+                         float(tol), int(maxit), ctypes.byref(iters), ctypes.byref(relres), _d(hist))
     return x, iters.value, relres.value, hist[: iters.value + 1].copy(), st
 
 

@@ -397,6 +397,53 @@ void nbo_apply_A(int Ex, int Ey, int Ez, int n, const double *D, const double *g
 }
 
 /* ------------------------------------------------------------------ */
+/* Jacobi preconditioner (the paper names preconditioned CG as future   */
+/* work, Sec. VII).  The diagonal of the element matrix A_e of Listing 1 */
+/* at local point p = (i,j,k) is sum over quadrature points of          */
+/* grad(phi_p)^T G grad(phi_p); d/dr phi_p is nonzero only on the line  */
+/* through p along r (value dxm1(a,i) at node a), and likewise for s, t, */
+/* so                                                                   */
+/*   A_e(p,p) = sum_a D(a,i)^2 g_rr(a,j,k) + sum_b D(b,j)^2 g_ss(i,b,k) */
+/*            + sum_c D(c,k)^2 g_tt(i,j,c)                               */
+/*            + 2 D(i,i) D(j,j) g_rs(p) + 2 D(i,i) D(k,k) g_rt(p)        */
+/*            + 2 D(j,j) D(k,k) g_st(p).                                 */
+/* ------------------------------------------------------------------ */
+void nbo_diag_e(int E, int n, const double *D, const double *gxyz, double *diag)
+{
+    const long n3 = (long)n * n * n;
+    for (long e = 0; e < E; e++) {
+        const double *g = gxyz + e * 6 * n3;
+        for (int k = 0; k < n; k++)
+        for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) {
+            long p = i + n * (j + (long)n * k);
+            double d = 0.0;
+            for (int a = 0; a < n; a++)
+                d = d + D[a * n + i] * D[a * n + i] * g[0 * n3 + a + n * (j + (long)n * k)];
+            for (int b = 0; b < n; b++)
+                d = d + D[b * n + j] * D[b * n + j] * g[3 * n3 + i + n * (b + (long)n * k)];
+            for (int c = 0; c < n; c++)
+                d = d + D[c * n + k] * D[c * n + k] * g[5 * n3 + i + n * (j + (long)n * c)];
+            d = d + 2.0 * D[i * n + i] * D[j * n + j] * g[1 * n3 + p]
+                  + 2.0 * D[i * n + i] * D[k * n + k] * g[2 * n3 + p]
+                  + 2.0 * D[j * n + j] * D[k * n + k] * g[4 * n3 + p];
+            diag[e * n3 + p] = d;
+        }
+    }
+}
+
+/* Inverse assembled diagonal: minv = 1 / dssum(diag_e) at unmasked points,
+ * 0 at Dirichlet points. */
+void nbo_jacobi_inverse(int Ex, int Ey, int Ez, int n, const double *D, const double *gxyz,
+                        const uint8_t *mask, double *minv)
+{
+    const long E = (long)Ex * Ey * Ez, n3 = (long)n * n * n;
+    nbo_diag_e((int)E, n, D, gxyz, minv);
+    nbo_dssum(Ex, Ey, Ez, n, minv);
+    for (long q = 0; q < E * n3; q++) minv[q] = mask[q] ? 1.0 / minv[q] : 0.0;
+}
+
+/* ------------------------------------------------------------------ */
 /* C6. Unpreconditioned conjugate gradient on local storage (Nekbone   */
 /* form; the paper solves Ax = f with CG, Sec. III, and uses no         */
 /* preconditioner, Sec. VII).                                            */
@@ -447,5 +494,62 @@ int nbo_cg(int Ex, int Ey, int Ez, int n, const double *D, const double *gxyz,
     if (iters_out) *iters_out = iters;
     if (relres_out) *relres_out = fnorm > 0.0 ? sqrt(rho) / fnorm : 0.0;
     free(r); free(p); free(w);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Jacobi-preconditioned CG (textbook PCG, e.g. Saad, Iterative Methods */
+/* for Sparse Linear Systems, Alg. 9.1) with z = minv .* r:             */
+/*   r = f - A x0, z = minv r, p = 0, rho_old = 1                       */
+/*   for it = 1..maxit:                                                  */
+/*     rho = <r,z>_c; stop if rho == 0 or (tol > 0 and                   */
+/*     sqrt(<r,r>_c / <f,f>_c) <= tol)                                   */
+/*     beta = (it == 1) ? 0 : rho / rho_old;  p = z + beta p             */
+/*     w = A p;  alpha = rho / <w,p>_c;  x += alpha p;  r -= alpha w     */
+/*     z = minv r;  rho_old = rho                                         */
+/* With minv = 1 this is nbo_cg step for step.  rr_hist (optional) gets */
+/* <r,r>_c per iteration (iters + 1 values).                             */
+/* ------------------------------------------------------------------ */
+int nbo_pcg(int Ex, int Ey, int Ez, int n, const double *D, const double *gxyz,
+            const uint8_t *mask, const double *minv, const double *f, double *x, double tol,
+            int maxit, int *iters_out, double *relres_out, double *rr_hist)
+{
+    const long E = (long)Ex * Ey * Ez, n3 = (long)n * n * n, npts = E * n3;
+    double *r = (double *)malloc(sizeof(double) * npts);
+    double *z = (double *)malloc(sizeof(double) * npts);
+    double *p = (double *)malloc(sizeof(double) * npts);
+    double *w = (double *)malloc(sizeof(double) * npts);
+    int status = 0, iters = 0;
+
+    nbo_apply_A(Ex, Ey, Ez, n, D, gxyz, mask, x, w);
+    for (long q = 0; q < npts; q++) { r[q] = f[q] - w[q]; z[q] = minv[q] * r[q]; p[q] = 0.0; }
+    double fnorm = sqrt(nbo_dot_c(Ex, Ey, Ez, n, f, f));
+    double rho_old = 1.0;
+    double rho = nbo_dot_c(Ex, Ey, Ez, n, r, z);
+    double rr = nbo_dot_c(Ex, Ey, Ez, n, r, r);
+    if (rr_hist) rr_hist[0] = rr;
+    for (int it = 1; it <= maxit; it++) {
+        if (rho == 0.0) break;
+        if (tol > 0.0 && sqrt(rr) / fnorm <= tol) break;
+        double beta = (it == 1) ? 0.0 : rho / rho_old;
+        for (long q = 0; q < npts; q++) p[q] = z[q] + beta * p[q];
+        nbo_apply_A(Ex, Ey, Ez, n, D, gxyz, mask, p, w);
+        double pap = nbo_dot_c(Ex, Ey, Ez, n, w, p);
+        if (!(pap > 0.0) || !isfinite(pap)) { status = 1; break; }
+        double alpha = rho / pap;
+        for (long q = 0; q < npts; q++) {
+            x[q] = x[q] + alpha * p[q];
+            r[q] = r[q] - alpha * w[q];
+            z[q] = minv[q] * r[q];
+        }
+        rho_old = rho;
+        rho = nbo_dot_c(Ex, Ey, Ez, n, r, z);
+        rr = nbo_dot_c(Ex, Ey, Ez, n, r, r);
+        iters = it;
+        if (rr_hist) rr_hist[it] = rr;
+    }
+    if (iters_out) *iters_out = iters;
+    if (relres_out) *relres_out = fnorm > 0.0 ? sqrt(rr) / fnorm : 0.0;
+    free(r); free(z); free(p); free(w);
     return status;
 }

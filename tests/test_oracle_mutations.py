@@ -14,6 +14,7 @@ import pytest
 import tests.test_oracle_ax as tax
 import tests.test_oracle_dssum_cg as tdc
 import tests.test_oracle_gll as tgl
+import tests.test_oracle_pcg as tpc
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -33,9 +34,13 @@ MUTATIONS = {
                             "for (long q = E * n3 - 1; q >= 0; q--) acc[gid[q]] = acc[gid[q]] + w[q];"),
     "mask_misses_z_faces": ("gy == 0 || gy == NY - 1 ||\n                          gz == 0 || gz == NZ - 1;",
                             "gy == 0 || gy == NY - 1;"),
-    "cg_beta_inverted": ("double beta = (it == 1) ? 0.0 : rho / rho_old;",
-                         "double beta = (it == 1) ? 0.0 : rho_old / rho;"),
-    "cg_residual_sign": ("r[q] = r[q] - alpha * w[q];", "r[q] = r[q] + alpha * w[q];"),
+    "cg_beta_inverted": ("double beta = (it == 1) ? 0.0 : rho / rho_old;\n        for (long q = 0; q < npts; q++) p[q] = r[q] + beta * p[q];",
+                         "double beta = (it == 1) ? 0.0 : rho_old / rho;\n        for (long q = 0; q < npts; q++) p[q] = r[q] + beta * p[q];"),
+    "cg_residual_sign": ("r[q] = r[q] - alpha * w[q];\n        }\n        rho_old = rho;\n        rho = nbo_dot_c(Ex, Ey, Ez, n, r, r);",
+                         "r[q] = r[q] + alpha * w[q];\n        }\n        rho_old = rho;\n        rho = nbo_dot_c(Ex, Ey, Ez, n, r, r);"),
+    "diag_drops_cross_term": ("+ 2.0 * D[j * n + j] * D[k * n + k] * g[4 * n3 + p];",
+                              ";"),
+    "pcg_z_from_w": ("z[q] = minv[q] * r[q];\n        }", "z[q] = minv[q] * w[q];\n        }"),
     "gid_wrong_local_index": ("long gy = (long)ey * (n - 1) + j;\n            long gz = (long)ez * (n - 1) + k;\n            gid[",
                               "long gy = (long)ey * (n - 1) + i;\n            long gz = (long)ez * (n - 1) + k;\n            gid["),
 }
@@ -52,6 +57,8 @@ PINS = [
     lambda o: tdc.test_dssum_canonical_order_bruteforce(o, (2, 2, 2), 3),
     lambda o: tdc.test_cg_matches_dense_solve(o, (2, 2, 2), 3),
     lambda o: tdc.test_cg_energy_error_decreases_and_fixed_iterations(o),
+    lambda o: tpc.test_diag_matches_bruteforce_element_matrix(o, 3),
+    lambda o: tpc.test_jacobi_pcg_dense_solve_and_iterations(o),
 ]
 
 
