@@ -166,7 +166,7 @@ nb_status nb_cg_solve_host(nb_ctx *ctx, const double *f_host, double *x_host,
                            double tol, int maxit, int *iters_out,
                            double *relres_out);
 
-/* rho_k = <r_k,r_k>_c of the last FP64 solve, k = 0..iters (host copy).
+/* <r_k,r_k>_c of the last FP64 solve, k = 0..iters (host copy).
  * Writes min(cap, iters+1) values, *count = iters + 1. */
 nb_status nb_cg_history(nb_ctx *ctx, double *rho_host, int cap, int *count);
 
@@ -227,6 +227,17 @@ nb_status nb_dssum_f32(nb_ctx *ctx, float *w_dev);
  * max_outer FP64 corrections (default 50).  The outer residual, every dot
  * product and norm, and the update x += d are FP64. */
 nb_status nb_set_mixed_params(nb_ctx *ctx, double inner_tol, int max_outer);
+
+/* Preconditioner of nb_cg_solve for NB_FP64 contexts: 0 = none (the
+ * paper's plain CG), 1 = Jacobi, the inverse of the assembled diagonal of A
+ * (computed on the device from D and gxyz, 0 at Dirichlet points).  With
+ * Jacobi the solve is PCG with z = minv r: rho = <r,z>_c drives beta and
+ * alpha, while the stopping test, relres and the history use <r,r>_c.
+ * Preconditioned CG is the paper's stated future work (Sec. VII). */
+nb_status nb_set_preconditioner(nb_ctx *ctx, int kind);
+
+/* Copy the Jacobi inverse diagonal (device, E*n^3 doubles). */
+nb_status nb_jacobi_diagonal(nb_ctx *ctx, double *minv_dev);
 
 /* Iterations of the last solve: for NB_FP64 CG iterations; for NB_MIXED
  * the total inner iterations and the number of outer corrections. */

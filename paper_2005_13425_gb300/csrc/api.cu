@@ -89,7 +89,7 @@ static bool aligned8(const void *p) { return ((uintptr_t)p & 7u) == 0; }
 static void free_ctx(nb_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    void *ptrs[] = {c->d_D, c->d_gxyz, c->d_mask, c->d_Df, c->d_gxyz_df, c->d_gxyz32,
+    void *ptrs[] = {c->d_D, c->d_gxyz, c->d_mask, c->d_Df, c->d_gxyz_df, c->d_gxyz32, c->d_minv,
                     c->d_r, c->d_p, c->d_w, c->d_x, c->d_partials, c->d_sc, c->d_hist,
                     c->d_r32, c->d_p32, c->d_w32, c->d_z32};
     for (void *p : ptrs)
@@ -440,6 +440,25 @@ nb_status nb_set_mixed_params(nb_ctx *c, double inner_tol, int max_outer) {
     c->mixed_inner_tol = inner_tol;
     c->mixed_max_outer = max_outer;
     return NB_OK;
+}
+
+nb_status nb_set_preconditioner(nb_ctx *c, int kind) {
+    NB_GUARD_BEGIN
+    if (!c) return fail(NB_ERR_ARG, "NULL context");
+    if (kind != 0 && kind != 1) return fail(NB_ERR_ARG, "preconditioner must be 0 (none) or 1 (Jacobi)");
+    if (kind == 1 && c->prec == NB_MIXED)
+        return fail(NB_ERR_STATE, "the Jacobi preconditioner applies to NB_FP64 contexts");
+    return set_preconditioner(c, kind);
+    NB_GUARD_END
+}
+
+nb_status nb_jacobi_diagonal(nb_ctx *c, double *minv_dev) {
+    NB_GUARD_BEGIN
+    if (!c || !minv_dev) return fail(NB_ERR_ARG, "NULL argument");
+    if (!c->d_minv) return fail(NB_ERR_STATE, "no Jacobi preconditioner set");
+    NB_CUDA(cudaMemcpyAsync(minv_dev, c->d_minv, sizeof(double) * c->m.npts, cudaMemcpyDeviceToDevice, c->stream));
+    return NB_OK;
+    NB_GUARD_END
 }
 
 nb_status nb_solve_stats(const nb_ctx *c, int *iters, int *outer) {

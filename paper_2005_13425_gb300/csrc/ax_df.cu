@@ -35,6 +35,7 @@ struct AxDfArgs {
     const double *r;      // MODE 1: residual
     double *p;            // MODE 1: search direction, updated in place
     double *x;            // MODE 1: iterate, receives the owed x += x_alpha p
+    const double *minv;   // MODE 1: Jacobi inverse diagonal or null
     const CgScalars *sc;  // MODE 1
     double *partials;     // MODE 1 fused: one <w,p> partial per CTA
     int fuse;             // MODE 1: zero box-face points, interior <w,p>
@@ -66,6 +67,7 @@ ax_df_kernel(AxDfArgs a, const __grid_constant__ typename DfConsts<N, EO>::type 
         io.r = MODE == 1 ? a.r + eb : nullptr;
         io.p = MODE == 1 ? a.p + eb : nullptr;
         io.x = MODE == 1 ? a.x + eb : nullptr;
+        io.minv = (MODE == 1 && a.minv) ? a.minv + eb : nullptr;
         io.w = a.w + eb;
         io.g = a.g + e * 6 * N3;
         int ex = 0, ey = 0, ez = 0;
@@ -158,6 +160,7 @@ static nb_status launch_df_nv(nb_ctx *c, const double *u, double *w, int mode) {
         args.r = c->d_r;
         args.p = c->d_p;
         args.x = c->d_x;
+        args.minv = c->d_minv;
         args.w = c->d_w;
         args.sc = c->d_sc;
         args.partials = c->d_partials;

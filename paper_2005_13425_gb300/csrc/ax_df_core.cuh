@@ -151,6 +151,7 @@ struct DfElemIO {
     const double *r;    // MODE 1: residual
     double *p;          // MODE 1: search direction (updated in place)
     double *x;          // MODE 1: iterate (owed update applied when xa != 0)
+    const double *minv; // MODE 1: Jacobi inverse diagonal (z = minv r), or null
     double *w;          // output
     const float2 *g;    // gxyz pairs [6][n^3] of the element, scaled by 2^-(gexp-1023)
 };
@@ -183,7 +184,8 @@ __device__ __forceinline__ void df_element(const DfElemIO &io, double beta, doub
             // x += alpha p of the previous iteration, then p = r + beta p
             const double pold = io.p[q];
             if (xa != 0.0) io.x[q] = fma(xa, pold, io.x[q]);
-            v = fma(beta, pold, io.r[q]);
+            const double z = io.minv ? io.r[q] * io.minv[q] : io.r[q];
+            v = fma(beta, pold, z);
             io.p[q] = v;
         } else {
             v = __ldg(io.u + q);

@@ -31,6 +31,7 @@ struct AxCgArgs {
     const double *r;      // residual
     double *p;            // search direction, updated in place
     double *x;            // iterate, receives the owed x += x_alpha p
+    const double *minv;   // Jacobi inverse diagonal (z = minv r) or null
     const CgScalars *sc;
     double *partials;     // fused: one <w,p> partial per CTA
     int fuse;             // zero box-face points and sum <w,p> over interior points
@@ -72,7 +73,8 @@ ax_fp64_kernel(const double *__restrict__ u, double *__restrict__ w,
             if (MODE == 1) {
                 const double pold = cg.p[base + q];
                 if (xa != 0.0) cg.x[base + q] = fma(xa, pold, cg.x[base + q]);
-                v = fma(beta, pold, cg.r[base + q]);
+                const double z = cg.minv ? cg.r[base + q] * cg.minv[base + q] : cg.r[base + q];
+                v = fma(beta, pold, z);
                 cg.p[base + q] = v;
             } else {
                 v = __ldg(u + base + q);
@@ -167,6 +169,7 @@ static nb_status launch_n(nb_ctx *c, const double *u, double *w, int mode) {
         cg.r = c->d_r;
         cg.p = c->d_p;
         cg.x = c->d_x;
+        cg.minv = c->d_minv;
         cg.sc = c->d_sc;
         cg.partials = c->d_partials;
         cg.fuse = c->fused_cg ? 1 : 0;

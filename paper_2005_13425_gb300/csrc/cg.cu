@@ -58,15 +58,16 @@ static int red_grid(const nb_ctx *c) {
 
 // MODE 0: *out = <a,b>_c.
 // MODE 1 (unfused solver step): pap = <w,p>_c, alpha = rho/pap.
-// MODE 2 (solver start): r = f - w, p = 0, rho = <r,r>_c, fnorm2 = <f,f>_c.
+// MODE 2 (solver start): r = f - w, p = 0, rho = <r,z>_c (z = minv r or r),
+//   rr = <r,r>_c, fnorm2 = <f,f>_c.
 template <int N, int MODE>
 __global__ void __launch_bounds__(kRedThreads)
 dot_kernel(const double *__restrict__ a, const double *__restrict__ b, double *__restrict__ rr,
            double *__restrict__ pp, Mesh m, double *partials, CgScalars *sc, double *out,
-           double *hist) {
+           double *hist, const double *__restrict__ minv) {
     constexpr int N3 = N * N * N;
     if (MODE == 1 && sc->done) return;
-    double acc0 = 0.0, acc1 = 0.0;
+    double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
     for (int64_t e = blockIdx.x; e < m.E; e += gridDim.x) {
         int ex, ey, ez;
         element_coords(e, m, ex, ey, ez);
@@ -83,18 +84,20 @@ dot_kernel(const double *__restrict__ a, const double *__restrict__ b, double *_
                 const int lg = log2_mult(i, j, k, ex, ey, ez, m);
                 acc0 = fma(scale_down_pow2(r, lg), r, acc0);
                 acc1 = fma(scale_down_pow2(f, lg), f, acc1);
+                if (minv) acc2 = fma(scale_down_pow2(r * minv[base + p], lg), r, acc2);
             } else {
                 acc0 = fma(a[base + p] * cw, b[base + p], acc0);
             }
         }
     }
     if (MODE == 2) {
-        double v[2] = {acc0, acc1}, tot[2];
-        if (!last_block_reduce<2>(v, partials, gridDim.x, blockIdx.x, gridDim.x, gridDim.x,
+        double v[3] = {acc0, acc1, acc2}, tot[3];
+        if (!last_block_reduce<3>(v, partials, gridDim.x, blockIdx.x, gridDim.x, gridDim.x,
                                   &sc->ticket, tot))
             return;
         if (threadIdx.x != 0) return;
-        sc->rho = tot[0];
+        sc->rr = tot[0];
+        sc->rho = minv ? tot[2] : tot[0];
         sc->rho_old = 1.0;
         sc->fnorm2 = tot[1];
         sc->beta = 0.0;
@@ -103,7 +106,7 @@ dot_kernel(const double *__restrict__ a, const double *__restrict__ b, double *_
         sc->status = 0;
         if (hist) hist[0] = tot[0];
         const bool conv = sc->tol > 0.0 && sqrt(tot[0]) / sqrt(tot[1]) <= sc->tol;
-        sc->done = (tot[0] == 0.0 || conv || sc->maxit == 0) ? 1 : 0;
+        sc->done = (sc->rho == 0.0 || conv || sc->maxit == 0) ? 1 : 0;
         return;
     }
     double v[1] = {acc0}, tot[1];
@@ -126,15 +129,16 @@ dot_kernel(const double *__restrict__ a, const double *__restrict__ b, double *_
     }
 }
 
-// r -= alpha w, rho = <r,r>_c, beta = rho/rho_old, convergence decision.
+// r -= alpha w, rr = <r,r>_c, rho = <r,z>_c (z = minv r with Jacobi, else
+// rho = rr), beta = rho/rho_old, convergence decision on rr.
 template <int N>
 __global__ void __launch_bounds__(kRedThreads)
 update_kernel(double *__restrict__ r, const double *__restrict__ w, Mesh m, double *partials,
-              CgScalars *sc, double *hist) {
+              CgScalars *sc, double *hist, const double *__restrict__ minv) {
     constexpr int N3 = N * N * N;
     if (sc->done) return;
     const double alpha = sc->alpha;
-    double acc = 0.0;
+    double acc = 0.0, accz = 0.0;
     for (int64_t e = blockIdx.x; e < m.E; e += gridDim.x) {
         int ex, ey, ez;
         element_coords(e, m, ex, ey, ez);
@@ -144,21 +148,25 @@ update_kernel(double *__restrict__ r, const double *__restrict__ w, Mesh m, doub
             const int i = q % N, j = (q / N) % N, k = q / (N * N);
             const double rn = fma(-alpha, w[base + q], r[base + q]);
             r[base + q] = rn;
-            acc = fma(scale_down_pow2(rn, log2_mult(i, j, k, ex, ey, ez, m)), rn, acc);
+            const int lg = log2_mult(i, j, k, ex, ey, ez, m);
+            acc = fma(scale_down_pow2(rn, lg), rn, acc);
+            if (minv) accz = fma(scale_down_pow2(rn * minv[base + q], lg), rn, accz);
         }
     }
-    double v[1] = {acc}, tot[1];
-    if (!last_block_reduce<1>(v, partials, 0, blockIdx.x, gridDim.x, gridDim.x, &sc->ticket, tot))
+    double v[2] = {acc, accz}, tot[2];
+    if (!last_block_reduce<2>(v, partials, gridDim.x, blockIdx.x, gridDim.x, gridDim.x, &sc->ticket, tot))
         return;
     if (threadIdx.x != 0) return;
-    const double rho = tot[0];
+    const double rr = tot[0];
+    const double rho = minv ? tot[1] : rr;
+    sc->rr = rr;
     sc->rho_old = sc->rho;
     sc->rho = rho;
     sc->beta = rho / sc->rho_old;
     const int it = sc->it + 1;
     sc->it = it;
-    hist[it] = rho;
-    const bool conv = sc->tol > 0.0 && sqrt(rho) / sqrt(sc->fnorm2) <= sc->tol;
+    hist[it] = rr;
+    const bool conv = sc->tol > 0.0 && sqrt(rr) / sqrt(sc->fnorm2) <= sc->tol;
     if (rho == 0.0 || conv || it >= sc->maxit) sc->done = 1;
 }
 
@@ -188,20 +196,22 @@ static void dot_launch(nb_ctx *c, int mode, const double *a, const double *b, do
     const int grid = red_grid(c);
     if (mode == 0)
         dot_kernel<N, 0><<<grid, kRedThreads, 0, c->stream>>>(a, b, nullptr, nullptr, c->m, c->d_partials,
-                                                             c->d_sc, out, nullptr);
+                                                             c->d_sc, out, nullptr, nullptr);
     else if (mode == 1)
         dot_kernel<N, 1><<<grid, kRedThreads, 0, c->stream>>>(c->d_w, c->d_p, nullptr, nullptr, c->m,
-                                                             c->d_partials, c->d_sc, nullptr, nullptr);
+                                                             c->d_partials, c->d_sc, nullptr, nullptr,
+                                                             nullptr);
     else
         dot_kernel<N, 2><<<grid, kRedThreads, 0, c->stream>>>(a, b, c->d_r, c->d_p, c->m, c->d_partials,
                                                              c->d_sc, nullptr,
-                                                             c->prec == NB_MIXED ? nullptr : c->d_hist);
+                                                             c->prec == NB_MIXED ? nullptr : c->d_hist,
+                                                             c->prec == NB_MIXED ? nullptr : c->d_minv);
 }
 
 template <int N>
 static void update_launch(nb_ctx *c) {
     update_kernel<N><<<red_grid(c), kRedThreads, 0, c->stream>>>(c->d_r, c->d_w, c->m, c->d_partials,
-                                                                c->d_sc, c->d_hist);
+                                                                c->d_sc, c->d_hist, c->d_minv);
 }
 
 static nb_status launch_dot(nb_ctx *c, int mode, const double *a, const double *b, double *out) {
@@ -371,10 +381,10 @@ nb_status cg_solve_fp64(nb_ctx *c, const double *f, double *x, double tol, int m
     const CgScalars &h = *c->h_sc;
     c->last_iters = h.it;
     if (iters) *iters = h.it;
-    const double rel = h.fnorm2 > 0.0 ? sqrt(h.rho) / sqrt(h.fnorm2) : 0.0;
+    const double rel = h.fnorm2 > 0.0 ? sqrt(h.rr) / sqrt(h.fnorm2) : 0.0;
     if (relres) *relres = rel;
     if (h.status == (int)NB_ERR_BREAKDOWN) return fail(NB_ERR_BREAKDOWN, "CG breakdown: <Ap,p>_c <= 0 or not finite");
-    if (tol > 0.0 && !(rel <= tol) && h.rho != 0.0)
+    if (tol > 0.0 && !(rel <= tol) && h.rr != 0.0)
         return fail(NB_ERR_NOT_CONVERGED, "CG did not reach the tolerance within maxit");
     return NB_OK;
 }
@@ -429,7 +439,7 @@ nb_status dot_c_noalloc(const Mesh &m, const double *a, const double *b, double 
     const int grid = (int)m.E;   // one CTA, hence one partial slot, per element
 #define CALL(NN)                                                                                   \
     dot_kernel<NN, 0><<<grid, kRedThreads, 0, stream>>>(a, b, nullptr, nullptr, m, s->partials,    \
-                                                       &s->sc, out, nullptr)
+                                                       &s->sc, out, nullptr, nullptr)
     NB_DISPATCH_N(m.n, CALL)
 #undef CALL
     NB_LAUNCH_CHECK("dot_kernel (allocation-free)");

@@ -80,6 +80,7 @@ eng_ax_head(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const i
             io.r = P.r + eb;
             io.p = P.p + eb;
             io.x = P.x + eb;
+            io.minv = nullptr;
             io.w = P.w + eb;
             io.g = P.g + e * 6 * N3;
             int ex, ey, ez;

@@ -46,7 +46,8 @@ struct Mesh {
 // ---------------------------------------------------------------- CG state
 // Device-resident scalars of one CG solve.
 struct CgScalars {
-    double rho;        // <r,r>_c of the current residual
+    double rho;        // <r,z>_c (z = r without a preconditioner, minv r with Jacobi)
+    double rr;         // <r,r>_c (convergence test and history)
     double rho_old;    // previous rho
     double alpha, beta;
     double pap;        // <w,p>_c
@@ -89,6 +90,7 @@ struct nb_ctx {
     double *d_r = nullptr, *d_p = nullptr, *d_w = nullptr, *d_x = nullptr;
     double *d_partials = nullptr;
     int partial_cap = 0;
+    double *d_minv = nullptr;           // Jacobi: 1/diag(A) (0 at Dirichlet points), or null
     nekgb::CgScalars *d_sc = nullptr;
     nekgb::CgScalars *h_sc = nullptr;   // pinned mirror
     double *d_hist = nullptr;
@@ -157,6 +159,7 @@ nb_status cg_solve_fp64(nb_ctx *c, const double *f, double *x, double tol, int m
 nb_status cg_solve_mixed(nb_ctx *c, const double *f, double *x, double tol, int maxit,
                          int *iters, double *relres);
 nb_status ensure_cg_workspace(nb_ctx *c);
+nb_status set_preconditioner(nb_ctx *c, int kind);   // precond.cu
 nb_status prepare_df(nb_ctx *c);   // double-float copies of D and gxyz
 bool centro_antisymmetric(const double *D, int n);
 nb_status prepare_fp32(nb_ctx *c); // fp32 copy of gxyz for the mixed solve

@@ -80,6 +80,7 @@ inner_start_kernel(const float *__restrict__ r, float *__restrict__ p, float *__
     if (!last_block_reduce<1>(v, partials, 0, blockIdx.x, gridDim.x, gridDim.x, &sc->ticket, tot)) return;
     if (threadIdx.x != 0) return;
     sc->rho = tot[0];
+    sc->rr = tot[0];
     sc->rho_old = 1.0;
     sc->fnorm2 = tot[0];
     sc->beta = 0.0;
@@ -245,7 +246,7 @@ nb_status cg_solve_mixed(nb_ctx *c, const double *f, double *x, double tol, int 
         if ((s = dot_start(c, f)) != NB_OK) return s;
         NB_CUDA(cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream));
         NB_CUDA(cudaStreamSynchronize(c->stream));
-        const double rho = c->h_sc->rho, fn2 = c->h_sc->fnorm2;
+        const double rho = c->h_sc->rr, fn2 = c->h_sc->fnorm2;
         rel = fn2 > 0.0 ? sqrt(rho) / sqrt(fn2) : 0.0;
         if (rho == 0.0 || (tol > 0.0 && rel <= tol)) {
             converged = true;

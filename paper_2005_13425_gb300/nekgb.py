@@ -82,6 +82,8 @@ _SIGS = {
     "nb_dssum_f32": [_vp, _vp],
     "nb_set_mixed_params": [_vp, ctypes.c_double, ctypes.c_int],
     "nb_solve_stats": [_vp, _ip, _ip],
+    "nb_set_preconditioner": [_vp, ctypes.c_int],
+    "nb_jacobi_diagonal": [_vp, _vp],
     "nb_engine_create": [ctypes.POINTER(_vp), ctypes.c_size_t, _vp],
     "nb_engine_destroy": [_vp],
     "nb_engine_footprint": [nb_box, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
@@ -295,6 +297,14 @@ def nb_dssum_f32(ctx, w):
 
 def nb_set_mixed_params(ctx, inner_tol: float = 1e-5, max_outer: int = 50):
     _check(load().nb_set_mixed_params(ctx, float(inner_tol), int(max_outer)), "nb_set_mixed_params")
+
+
+def nb_set_preconditioner(ctx, kind: int):
+    _check(load().nb_set_preconditioner(ctx, int(kind)), "nb_set_preconditioner")
+
+
+def nb_jacobi_diagonal(ctx, minv):
+    _check(load().nb_jacobi_diagonal(ctx, _ptr(minv, "torch.float64")), "nb_jacobi_diagonal")
 
 
 def nb_solve_stats(ctx):
