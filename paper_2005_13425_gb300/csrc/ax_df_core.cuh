@@ -178,21 +178,38 @@ __device__ __forceinline__ void df_element(const DfElemIO &io, double beta, doub
     const int t = threadIdx.x;
     // ---- stage the element (raw FP64 first, to find its scale)
     int emax = 0;
-    for (int q = t; q < N3; q += T) {
-        double v;
-        if (MODE == 1) {
-            // x += alpha p of the previous iteration, then p = r + beta p
-            const double pold = io.p[q];
-            if (xa != 0.0) io.x[q] = fma(xa, pold, io.x[q]);
-            const double z = io.minv ? io.r[q] * io.minv[q] : io.r[q];
-            v = fma(beta, pold, z);
-            io.p[q] = v;
-        } else {
-            v = __ldg(io.u + q);
-        }
+    // x += alpha p of the previous iteration, then p = z + beta p; the
+    // preconditioner and owed-update branches are uniform, so they are taken
+    // outside the point loops
+    auto stage = [&](double v, int q) {
         raw[q] = v;
         const int exb = (int)((__double_as_longlong(v) >> 52) & 0x7ff);
         emax = exb > emax ? exb : emax;
+    };
+    if (MODE == 0) {
+        for (int q = t; q < N3; q += T) stage(__ldg(io.u + q), q);
+    } else if (io.minv) {
+        for (int q = t; q < N3; q += T) {
+            const double pold = io.p[q];
+            if (xa != 0.0) io.x[q] = fma(xa, pold, io.x[q]);
+            const double v = fma(beta, pold, io.r[q] * io.minv[q]);
+            io.p[q] = v;
+            stage(v, q);
+        }
+    } else if (xa != 0.0) {
+        for (int q = t; q < N3; q += T) {
+            const double pold = io.p[q];
+            io.x[q] = fma(xa, pold, io.x[q]);
+            const double v = fma(beta, pold, io.r[q]);
+            io.p[q] = v;
+            stage(v, q);
+        }
+    } else {
+        for (int q = t; q < N3; q += T) {
+            const double v = fma(beta, io.p[q], io.r[q]);
+            io.p[q] = v;
+            stage(v, q);
+        }
     }
     emax = __reduce_max_sync(0xffffffffu, emax);
     if ((t & 31) == 0) atomicMax(s_emax, emax);

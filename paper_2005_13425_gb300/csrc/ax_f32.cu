@@ -7,6 +7,7 @@
 // parameters (constant-bank operands); a pointwise pass contracts with the
 // six geometric factors; the transposed derivatives go to three partial
 // arrays that a final pass adds.  Plain FP32 fused multiply-adds.
+#include "df.cuh"
 #include "internal.cuh"
 #include "reduce.cuh"
 
@@ -46,6 +47,21 @@ __device__ __forceinline__ int f32_line_of(int task, int &stride) {
     return a0 + N * a1;
 }
 
+// Asynchronous global->shared copies (cp.async, no register staging): the
+// element's geometric factors stream into shared memory while the forward
+// derivatives are computed.  16-byte chunks when the slab is 16-byte
+// aligned (n even), 4-byte otherwise.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // MODE 0: w = ax_e(u).  MODE 1: inner CG head (x += x_alpha p, p = r + beta
 // p, w = ax_e(p), box faces zeroed, element-interior <w,p> per CTA).
 template <int N, int MODE>
@@ -53,12 +69,13 @@ __global__ void __launch_bounds__(ax_f32_threads(N))
 ax_f32_kernel(AxF32Args a, const __grid_constant__ F32Mat<N> D) {
     constexpr int N2 = N * N, N3 = N * N * N;
     constexpr int T = ax_f32_threads(N);
-    extern __shared__ float smf[];
+    extern __shared__ __align__(16) float smf[];
     float *U = smf, *W0 = smf + N3, *W1 = smf + 2 * N3, *W2 = smf + 3 * N3;
     float *P1 = smf + 4 * N3, *P2 = smf + 5 * N3;
+    float *G = smf + ((6 * N3 + 3) / 4) * 4;   // 6 N3 geometric factors, 16-byte aligned
     __shared__ double red[32];
     float beta = 0.f, xa = 0.f;
-    double dot = 0.0;
+    dfa::Acc32 dot;
     if (MODE == 1) {
         if (a.sc->done) return;
         beta = a.sc->it == 0 ? 0.f : (float)a.sc->beta;
@@ -79,6 +96,15 @@ ax_f32_kernel(AxF32Args a, const __grid_constant__ F32Mat<N> D) {
             }
             U[q] = v;
         }
+        {   // prefetch this element's gxyz (consumed after the forward phase)
+            const float *gsrc = a.g + e * 6 * N3;
+            if ((N3 % 4) == 0) {
+                for (int q = t; q < 6 * N3 / 4; q += T) cp_async16(G + 4 * q, gsrc + 4 * q);
+            } else {
+                for (int q = t; q < 6 * N3; q += T) cp_async4(G + q, gsrc + q);
+            }
+            cp_async_commit();
+        }
         __syncthreads();
         for (int task = t; task < 3 * N2; task += T) {
             int stride;
@@ -95,12 +121,12 @@ ax_f32_kernel(AxF32Args a, const __grid_constant__ F32Mat<N> D) {
                 Wd[base + m * stride] = acc;
             }
         }
+        cp_async_wait_all();
         __syncthreads();
-        const float *g = a.g + e * 6 * N3;
         for (int q = t; q < N3; q += T) {
             const float wr = W0[q], ws = W1[q], wt = W2[q];
-            const float g0 = __ldg(g + q), g1 = __ldg(g + N3 + q), g2 = __ldg(g + 2 * N3 + q);
-            const float g3 = __ldg(g + 3 * N3 + q), g4 = __ldg(g + 4 * N3 + q), g5 = __ldg(g + 5 * N3 + q);
+            const float g0 = G[q], g1 = G[N3 + q], g2 = G[2 * N3 + q];
+            const float g3 = G[3 * N3 + q], g4 = G[4 * N3 + q], g5 = G[5 * N3 + q];
             W0[q] = fmaf(g0, wr, fmaf(g1, ws, g2 * wt));
             W1[q] = fmaf(g1, wr, fmaf(g3, ws, g4 * wt));
             W2[q] = fmaf(g2, wr, fmaf(g4, ws, g5 * wt));
@@ -132,14 +158,14 @@ ax_f32_kernel(AxF32Args a, const __grid_constant__ F32Mat<N> D) {
                 if (on_box_face(i, j, k, ex, ey, ez, a.m))
                     wv = 0.f;
                 else if (i > 0 && i < N - 1 && j > 0 && j < N - 1 && k > 0 && k < N - 1)
-                    dot = fma((double)wv, (double)a.p[eb + q], dot);
+                    dot.add_prod(wv, a.p[eb + q]);
             }
             a.w[eb + q] = wv;
         }
         __syncthreads();
     }
     if (MODE == 1) {
-        const double b = block_sum(dot, red);
+        const double b = block_sum(dot.value(), red);
         if (t == 0) a.partials[blockIdx.x] = b;
     }
 }
@@ -147,7 +173,7 @@ ax_f32_kernel(AxF32Args a, const __grid_constant__ F32Mat<N> D) {
 template <int N>
 static nb_status launch_f32_n(nb_ctx *c, const float *u, float *w, int mode) {
     constexpr int T = ax_f32_threads(N);
-    const size_t smem = sizeof(float) * 6 * N * N * N;
+    const size_t smem = sizeof(float) * (((6 * N * N * N + 3) / 4) * 4 + 6 * N * N * N);
     static bool configured[2] = {false, false};
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);

@@ -129,16 +129,13 @@ dot_kernel(const double *__restrict__ a, const double *__restrict__ b, double *_
     }
 }
 
-// r -= alpha w, rr = <r,r>_c, rho = <r,z>_c (z = minv r with Jacobi, else
-// rho = rr), beta = rho/rho_old, convergence decision on rr.
-template <int N>
-__global__ void __launch_bounds__(kRedThreads)
-update_kernel(double *__restrict__ r, const double *__restrict__ w, Mesh m, double *partials,
-              CgScalars *sc, double *hist, const double *__restrict__ minv) {
+// Body of the update: r -= alpha w over this CTA's elements, accumulating
+// <r,r>_c and, with PRE, <r, minv r>_c (shared nodes weighted 1/multiplicity).
+template <int N, bool PRE>
+__device__ __forceinline__ void update_body(double *__restrict__ r, const double *__restrict__ w, const Mesh &m,
+                                            double alpha, const double *__restrict__ minv, double &acc,
+                                            double &accz) {
     constexpr int N3 = N * N * N;
-    if (sc->done) return;
-    const double alpha = sc->alpha;
-    double acc = 0.0, accz = 0.0;
     for (int64_t e = blockIdx.x; e < m.E; e += gridDim.x) {
         int ex, ey, ez;
         element_coords(e, m, ex, ey, ez);
@@ -150,15 +147,36 @@ update_kernel(double *__restrict__ r, const double *__restrict__ w, Mesh m, doub
             r[base + q] = rn;
             const int lg = log2_mult(i, j, k, ex, ey, ez, m);
             acc = fma(scale_down_pow2(rn, lg), rn, acc);
-            if (minv) accz = fma(scale_down_pow2(rn * minv[base + q], lg), rn, accz);
+            if (PRE) accz = fma(scale_down_pow2(rn * minv[base + q], lg), rn, accz);
         }
     }
-    double v[2] = {acc, accz}, tot[2];
-    if (!last_block_reduce<2>(v, partials, gridDim.x, blockIdx.x, gridDim.x, gridDim.x, &sc->ticket, tot))
-        return;
+}
+
+// r -= alpha w, rr = <r,r>_c, rho = <r,z>_c (z = minv r with Jacobi, else
+// rho = rr), beta = rho/rho_old, convergence decision on rr.  PRE selects
+// the Jacobi form at compile time so the plain kernel carries none of it.
+template <int N, bool PRE>
+__global__ void __launch_bounds__(kRedThreads)
+update_kernel(double *__restrict__ r, const double *__restrict__ w, Mesh m, double *partials,
+              CgScalars *sc, double *hist, const double *__restrict__ minv) {
+    if (sc->done) return;
+    const double alpha = sc->alpha;
+    double acc = 0.0, accz = 0.0, rr, rho;
+    update_body<N, PRE>(r, w, m, alpha, minv, acc, accz);
+    if (PRE) {
+        double v[2] = {acc, accz}, tot[2];
+        if (!last_block_reduce<2>(v, partials, gridDim.x, blockIdx.x, gridDim.x, gridDim.x, &sc->ticket, tot))
+            return;
+        rr = tot[0];
+        rho = tot[1];
+    } else {
+        double v[1] = {acc}, tot[1];
+        if (!last_block_reduce<1>(v, partials, 0, blockIdx.x, gridDim.x, gridDim.x, &sc->ticket, tot))
+            return;
+        rr = tot[0];
+        rho = rr;
+    }
     if (threadIdx.x != 0) return;
-    const double rr = tot[0];
-    const double rho = minv ? tot[1] : rr;
     sc->rr = rr;
     sc->rho_old = sc->rho;
     sc->rho = rho;
@@ -210,8 +228,13 @@ static void dot_launch(nb_ctx *c, int mode, const double *a, const double *b, do
 
 template <int N>
 static void update_launch(nb_ctx *c) {
-    update_kernel<N><<<red_grid(c), kRedThreads, 0, c->stream>>>(c->d_r, c->d_w, c->m, c->d_partials,
-                                                                c->d_sc, c->d_hist, c->d_minv);
+    if (c->d_minv)
+        update_kernel<N, true><<<red_grid(c), kRedThreads, 0, c->stream>>>(c->d_r, c->d_w, c->m, c->d_partials,
+                                                                          c->d_sc, c->d_hist, c->d_minv);
+    else
+        update_kernel<N, false><<<red_grid(c), kRedThreads, 0, c->stream>>>(c->d_r, c->d_w, c->m,
+                                                                           c->d_partials, c->d_sc, c->d_hist,
+                                                                           nullptr);
 }
 
 static nb_status launch_dot(nb_ctx *c, int mode, const double *a, const double *b, double *out) {

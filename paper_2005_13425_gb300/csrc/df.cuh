@@ -79,6 +79,22 @@ __device__ __forceinline__ float2 add_acc(const Acc &P, const Acc &Q, float sgn)
     return make_float2(h, l);
 }
 
+// Compensated FP32 accumulation of products of floats (Dot2 on single
+// values): s + c carries sum(a*b) to about 2^-47 relative, with FP32
+// instructions only.  value() returns the FP64 total.
+struct Acc32 {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = __fmaf_rn(a, b, -p);
+        float t, err;
+        two_sum(s, p, t, err);
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // Split a double into a normalised pair: h = fl32(x), l = fl32(x - h).
 // x - h is exact in FP64, so h + l carries 48 bits of x.
 __device__ __forceinline__ float2 split(double x) {

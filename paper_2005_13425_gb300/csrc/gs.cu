@@ -8,6 +8,9 @@
 // read), so the kernel moves just the interface values.  Each node adds its
 // copies from +0.0 in ascending element order and writes the sum back to
 // every copy, which makes the result bit-for-bit independent of the launch.
+#include <type_traits>
+
+#include "df.cuh"
 #include "gs_nodes.cuh"
 #include "internal.cuh"
 #include "reduce.cuh"
@@ -24,7 +27,11 @@ __global__ void dssum_kernel(T *__restrict__ w, const T *__restrict__ p, Mesh m,
                              int cy, int cz, CgScalars *sc, double *partials, int slot0) {
     if (sc && sc->done) return;
     const int total = cx + cy + cz;
+    // <w,p>_c share: FP64 for FP64 fields; compensated FP32 (exact products,
+    // compensated sums: FP64-class accuracy on the FP32 pipe) for FP32 fields
+    constexpr bool F32 = std::is_same<T, float>::value;
     double dot = 0.0;
+    dfa::Acc32 dot32;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
         int gx, gy, gz;
         shared_node(q, m, cx, cy, gx, gy, gz);
@@ -39,7 +46,13 @@ __global__ void dssum_kernel(T *__restrict__ w, const T *__restrict__ p, Mesh m,
             const T s = plus_zero(a0) + a1;
             w[idx[0]] = s;
             w[idx[1]] = s;
-            if (CG) dot = node_dot(dot, s, 1, (double)p[idx[0]] + (double)p[idx[1]]);
+            if constexpr (CG && F32) {
+                const float sc = s * 0.5f;
+                dot32.add_prod(sc, p[idx[0]]);
+                dot32.add_prod(sc, p[idx[1]]);
+            } else if constexpr (CG) {
+                dot = node_dot(dot, s, 1, (double)p[idx[0]] + (double)p[idx[1]]);
+            }
         } else if (c == 4) {
             T a[4];
 #pragma unroll
@@ -49,7 +62,11 @@ __global__ void dssum_kernel(T *__restrict__ w, const T *__restrict__ p, Mesh m,
             for (int k = 1; k < 4; k++) s = s + a[k];
 #pragma unroll
             for (int k = 0; k < 4; k++) w[idx[k]] = s;
-            if (CG) {
+            if constexpr (CG && F32) {
+                const float sc = s * 0.25f;
+#pragma unroll
+                for (int k = 0; k < 4; k++) dot32.add_prod(sc, p[idx[k]]);
+            } else if constexpr (CG) {
                 double ps = (double)p[idx[0]];
 #pragma unroll
                 for (int k = 1; k < 4; k++) ps += (double)p[idx[k]];
@@ -64,7 +81,11 @@ __global__ void dssum_kernel(T *__restrict__ w, const T *__restrict__ p, Mesh m,
             for (int k = 1; k < 8; k++) s = s + a[k];
 #pragma unroll
             for (int k = 0; k < 8; k++) w[idx[k]] = s;
-            if (CG) {
+            if constexpr (CG && F32) {
+                const float sc = s * 0.125f;
+#pragma unroll
+                for (int k = 0; k < 8; k++) dot32.add_prod(sc, p[idx[k]]);
+            } else if constexpr (CG) {
                 double ps = (double)p[idx[0]];
 #pragma unroll
                 for (int k = 1; k < 8; k++) ps += (double)p[idx[k]];
@@ -72,6 +93,7 @@ __global__ void dssum_kernel(T *__restrict__ w, const T *__restrict__ p, Mesh m,
             }
         }
     }
+    if constexpr (F32) dot += dot32.value();
     if (CG) {
         double v[1] = {dot}, tot[1];
         if (!last_block_reduce<1>(v, partials, 0, slot0 + blockIdx.x, slot0 + gridDim.x, gridDim.x,

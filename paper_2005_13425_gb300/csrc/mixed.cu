@@ -17,6 +17,7 @@
 #include <math.h>
 #include <stdlib.h>
 
+#include "df.cuh"
 #include "internal.cuh"
 #include "reduce.cuh"
 
@@ -62,7 +63,7 @@ __global__ void __launch_bounds__(kT)
 inner_start_kernel(const float *__restrict__ r, float *__restrict__ p, float *__restrict__ x, Mesh m,
                    double *partials, CgScalars *sc) {
     constexpr int N3 = N * N * N;
-    double acc = 0.0;
+    dfa::Acc32 acc;   // exact products, compensated sums (FP64-class <r,r>_c)
     for (int64_t e = blockIdx.x; e < m.E; e += gridDim.x) {
         int ex, ey, ez;
         element_coords(e, m, ex, ey, ez);
@@ -70,13 +71,14 @@ inner_start_kernel(const float *__restrict__ r, float *__restrict__ p, float *__
 #pragma unroll 4
         for (int q = threadIdx.x; q < N3; q += kT) {
             const int i = q % N, j = (q / N) % N, k = q / (N * N);
-            const double rv = (double)r[base + q];
+            const float rv = r[base + q];
             p[base + q] = 0.f;
             x[base + q] = 0.f;
-            acc = fma(scale_down_pow2(rv, log2_mult(i, j, k, ex, ey, ez, m)), rv, acc);
+            const float cw = __uint_as_float((unsigned)(127 - log2_mult(i, j, k, ex, ey, ez, m)) << 23);  // 2^-lg
+            acc.add_prod(rv * cw, rv);
         }
     }
-    double v[1] = {acc}, tot[1];
+    double v[1] = {acc.value()}, tot[1];
     if (!last_block_reduce<1>(v, partials, 0, blockIdx.x, gridDim.x, gridDim.x, &sc->ticket, tot)) return;
     if (threadIdx.x != 0) return;
     sc->rho = tot[0];
@@ -98,7 +100,7 @@ inner_update_kernel(float *__restrict__ r, const float *__restrict__ w, Mesh m, 
     constexpr int N3 = N * N * N;
     if (sc->done) return;
     const float alpha = (float)sc->alpha;
-    double acc = 0.0;
+    dfa::Acc32 acc;   // exact products, compensated sums (FP64-class <r,r>_c)
     for (int64_t e = blockIdx.x; e < m.E; e += gridDim.x) {
         int ex, ey, ez;
         element_coords(e, m, ex, ey, ez);
@@ -108,11 +110,11 @@ inner_update_kernel(float *__restrict__ r, const float *__restrict__ w, Mesh m, 
             const int i = q % N, j = (q / N) % N, k = q / (N * N);
             const float rn = fmaf(-alpha, w[base + q], r[base + q]);
             r[base + q] = rn;
-            const double rv = (double)rn;
-            acc = fma(scale_down_pow2(rv, log2_mult(i, j, k, ex, ey, ez, m)), rv, acc);
+            const float cw = __uint_as_float((unsigned)(127 - log2_mult(i, j, k, ex, ey, ez, m)) << 23);  // 2^-lg
+            acc.add_prod(rn * cw, rn);
         }
     }
-    double v[1] = {acc}, tot[1];
+    double v[1] = {acc.value()}, tot[1];
     if (!last_block_reduce<1>(v, partials, 0, blockIdx.x, gridDim.x, gridDim.x, &sc->ticket, tot)) return;
     if (threadIdx.x != 0) return;
     const double rho = tot[0];
