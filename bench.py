@@ -387,25 +387,39 @@ def run_gpu(args, rank, world, local):
     hbm, _, peak_src = metrics.measured_peaks(ROOT)
     ax = kern["ax_e"]
     ax_avg_ms = ax["ms_total"] / max(ax["launches"], 1)
-    ax_bytes = metrics.ax_bytes_per_point(8) * D
-    ax_flops = metrics.ax_flops_per_point(NGLL) * D
-    ach_gbs = ax_bytes / (ax_avg_ms * 1e-3) / 1e9
-    ach_tf = ax_flops / (ax_avg_ms * 1e-3) / 1e12
-    hbm_frac = ach_gbs / hbm
-    alu_frac = ach_tf / metrics.NOMINAL_FP64_TFLOPS
-    total_kernel_ms = sum(v["ms_total"] for v in kern.values())
+    ax_bytes = metrics.cg_head_bytes_per_point(8) * D
     variant = nekgb.nb_get_info(ctx)["ax_variant"]
+    double_float = variant in (0, 2)      # automatic selection picks the double-float kernel at n = 10
+    ach_gbs = ax_bytes / (ax_avg_ms * 1e-3) / 1e9
+    hbm_frac = ach_gbs / hbm
+    total_kernel_ms = sum(v["ms_total"] for v in kern.values())
+    traffic = None
+    if double_float:
+        traffic = metrics.recorded_traffic(
+            os.path.join(ROOT, "profiles", "cg_head_ax_df_e4096_n10_traffic.md"),
+            metrics.source_digest(os.path.join(ROOT, "paper_2005_13425_gb300", "csrc")))
     roof_hbm = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm, "unit": "GB/s",
-                "frac": hbm_frac, "traffic": None,
-                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-                "kernel": "ax_e", "algorithmic_bytes_per_launch": ax_bytes,
+                "frac": hbm_frac, "traffic": traffic,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, of {peak_src})",
+                "kernel": "ax_e (CG head)", "algorithmic_bytes_per_launch": ax_bytes,
                 "avg_launch_ms": ax_avg_ms, "launches": ax["launches"]}
-    roof_alu = {"bound": "alu", "achieved": ach_tf, "peak": metrics.NOMINAL_FP64_TFLOPS,
-                "unit": "TFLOP/s", "frac": alu_frac, "traffic": None,
-                "peak_source": "recipe nominal GB300 FP64 1.25 TFLOP/s",
-                "kernel": "ax_e", "algorithmic_flops_per_launch": ax_flops,
-                "avg_launch_ms": ax_avg_ms, "launches": ax["launches"]}
-    roofline = roof_hbm if hbm_frac >= alu_frac else roof_alu
+    if double_float:
+        # the double-float ax_e runs on the FP32 pipe: its ALU bound is the
+        # FP32 instruction rate, its work the algorithm's FP32 instructions
+        ops = metrics.df_fp32_ops_per_point(NGLL) * D
+        ach = ops / (ax_avg_ms * 1e-3) / 1e12
+        roof_alu = {"bound": "alu", "achieved": ach, "peak": metrics.FP32_PEAK_TOPS,
+                    "unit": "T FP32 instr/s", "frac": ach / metrics.FP32_PEAK_TOPS, "traffic": traffic,
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (derived, nominal clock)",
+                    "kernel": "ax_e (CG head)", "algorithmic_fp32_instr_per_launch": ops,
+                    "avg_launch_ms": ax_avg_ms, "launches": ax["launches"]}
+    else:
+        ach = metrics.ax_flops_per_point(NGLL) * D / (ax_avg_ms * 1e-3) / 1e12
+        roof_alu = {"bound": "alu", "achieved": ach, "peak": metrics.NOMINAL_FP64_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / metrics.NOMINAL_FP64_TFLOPS, "traffic": None,
+                    "peak_source": "nominal GB300 FP64 1.25 TFLOP/s",
+                    "kernel": "ax_e (CG head)", "avg_launch_ms": ax_avg_ms, "launches": ax["launches"]}
+    roofline = roof_hbm if hbm_frac >= roof_alu["frac"] else roof_alu
     other_roofline = roof_alu if roofline is roof_hbm else roof_hbm
 
     line = {
@@ -446,15 +460,22 @@ def run_gpu(args, rank, world, local):
         line["batched"] = workloads.batched_run(nekgb, stream, batch, iters=100)
         line["batched"]["config"] = ("256 box problems, E log-uniform in [64, 4096] rounded to box dims, "
                                      "n from {6, 8, 10, 12}, FP64-accurate, 100 fixed CG iterations")
+        line["batched_mixed"] = workloads.batched_run(nekgb, stream, batch, iters=100, sequential=False,
+                                                      prec=nekgb.NB_MIXED)
+        line["batched_mixed"]["config"] = ("the same 256 problems, mixed precision (FP32 inner CG, FP64 "
+                                           "defect correction), 100 inner iterations")
         reqs = workloads.serving_requests(args.serve_requests, seed=5)
         arena = 48 << 30
         its = workloads.measure_iterations(nekgb, stream, reqs, arena)
         cap = line["batched"]["gdofs"] * 1e9
-        line["serving"] = [workloads.serving_run(nekgb, stream, reqs, u, cap, its, arena)
-                           for u in (0.5, 0.95)]
-        for srv in line["serving"]:
-            srv["config"] = (f"{len(reqs)} requests, Poisson arrivals, E log-uniform in [64, 32768], "
-                             "n from {6, 8, 10, 12}, tol 1e-8 or 1e-10, FP64-accurate, 48 GiB arena")
+        line["serving"] = []
+        for u in (0.5, 0.95, 2.0):
+            for prec in (nekgb.NB_FP64, nekgb.NB_MIXED):
+                srv = workloads.serving_run(nekgb, stream, reqs, u, cap, its, arena, prec=prec)
+                srv["config"] = (f"{len(reqs)} requests, Poisson arrivals at {u} x the FP64 batched capacity, "
+                                 "E log-uniform in [64, 32768], n from {6, 8, 10, 12}, tol 1e-8 or 1e-10, "
+                                 "48 GiB arena")
+                line["serving"].append(srv)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     nekgb.nb_destroy(ctx)

@@ -223,7 +223,7 @@ nb_status nb_ax_f32(nb_ctx *ctx, const float *u_dev, float *w_dev);
 nb_status nb_dssum_f32(nb_ctx *ctx, float *w_dev);
 
 /* Mixed-precision defect correction (NB_MIXED): the inner FP32 CG stops at
- * relative residual inner_tol (default 1e-5, 0 < inner_tol < 1); at most
+ * relative residual inner_tol (default 1e-4, 0 < inner_tol < 1); at most
  * max_outer FP64 corrections (default 50).  The outer residual, every dot
  * product and norm, and the update x += d are FP64. */
 nb_status nb_set_mixed_params(nb_ctx *ctx, double inner_tol, int max_outer);
@@ -256,9 +256,16 @@ nb_status nb_set_ax_variant(nb_ctx *ctx, int variant);
 typedef struct nb_engine nb_engine;  /* opaque; owns a device arena */
 
 /* One solve request: the synthetic box problem of nb_setup_box (mesh, n,
- * perturbation amp * s[d]) with right-hand side f, solved by FP64-accurate
- * CG from x0 = 0 to relative residual tol (tol <= 0: exactly maxit
- * iterations). */
+ * perturbation amp * s[d]) with right-hand side f, solved from x0 = 0 to
+ * relative residual tol.
+ *   prec = NB_FP64: FP64-accurate CG; tol <= 0 runs exactly maxit
+ *     iterations.
+ *   prec = NB_MIXED: defect correction around an FP32 inner CG (as
+ *     nb_cg_solve on an NB_MIXED context): the FP64 residual f - A x decides
+ *     convergence; each inner solve runs to relative residual inner_tol
+ *     (<= 0: 1e-4); maxit bounds the inner iterations in total; at most 50
+ *     outer corrections.
+ * Zero-initialise the struct: prec = 0 is NB_FP64. */
 typedef struct {
     nb_box mesh;
     int n;
@@ -266,6 +273,8 @@ typedef struct {
     double s[3];
     double tol;
     int maxit;
+    nb_precision prec;
+    double inner_tol;
 } nb_request;
 
 /* Create an engine with a device arena of arena_bytes (>= 1 MiB) on
@@ -273,9 +282,12 @@ typedef struct {
 nb_status nb_engine_create(nb_engine **out, size_t arena_bytes, void *cuda_stream);
 nb_status nb_engine_destroy(nb_engine *eng);
 
-/* Bytes of arena a request of this mesh and n needs (gxyz pairs, four CG
- * vectors and reduction partials), the admission criterion. */
-nb_status nb_engine_footprint(nb_box mesh, int n, size_t *bytes);
+/* Bytes of arena a request of this mesh, n and precision needs, the
+ * admission criterion.  NB_FP64: gxyz pairs (48 B/point), four FP64 CG
+ * vectors and reduction partials.  NB_MIXED: gxyz pairs and FP32 gxyz
+ * (72 B/point), three FP64 vectors (f, w, x), four FP32 vectors and
+ * partials. */
+nb_status nb_engine_footprint(nb_box mesh, int n, nb_precision prec, size_t *bytes);
 
 /* Admit a request: builds its geometry in the arena, copies f (device,
  * E*n^3 doubles, local storage; continuous and masked) and starts its solve.
@@ -294,9 +306,12 @@ nb_status nb_engine_submit_unique(nb_engine *eng, const nb_request *req, const d
                                   int *id_out);
 
 /* Advance every active request by `iters` CG iterations (rounded up to a
- * multiple of 8): per iteration, one launch per kernel and per distinct n
- * covers all active requests of that n; the iterations are replayed from a
- * captured CUDA graph.  Finished requests are skipped.  Blocks until done. */
+ * multiple of 8; for NB_MIXED requests, inner iterations): per iteration,
+ * one launch per kernel and per distinct (n, precision) covers all active
+ * requests of that kind; the iterations are replayed from a captured CUDA
+ * graph.  Each group of 8 starts with the outer pass of the NB_MIXED
+ * requests whose inner solve ended.  Finished requests are skipped.  Blocks
+ * until done. */
 nb_status nb_engine_step(nb_engine *eng, int iters);
 
 /* State of a request after the last step: *done = 1 once it converged, hit
@@ -304,6 +319,10 @@ nb_status nb_engine_step(nb_engine *eng, int iters);
  * and the solve status (NB_OK, NB_ERR_NOT_CONVERGED, NB_ERR_BREAKDOWN). */
 nb_status nb_engine_poll(nb_engine *eng, int id, int *done, int *iters, double *relres,
                          int *status);
+
+/* Precision of a request and, for NB_MIXED, the outer corrections so far
+ * (the count of FP64 residual passes that started an inner solve). */
+nb_status nb_engine_request_info(nb_engine *eng, int id, int *prec, int *outer);
 
 /* Copy the request's solution to x_dev (device, E*n^3 doubles; NULL to
  * drop it) and free its slot and arena space.  Blocks until done. */

@@ -117,6 +117,10 @@ static nb_status new_ctx(nb_ctx **out, nb_box mesh, int n, nb_precision prec, vo
     c->prec = prec;
     c->stream = (cudaStream_t)stream;
     c->ax_variant = 0;
+    {
+        const char *st = getenv("NEKGB_F32_STAGED");
+        c->f32_plain = st && st[0] == '0';
+    }
     *out = c;
     return NB_OK;
 }

@@ -7,16 +7,11 @@
 // parameters (constant-bank operands); a pointwise pass contracts with the
 // six geometric factors; the transposed derivatives go to three partial
 // arrays that a final pass adds.  Plain FP32 fused multiply-adds.
-#include "df.cuh"
+#include "ax_f32_core.cuh"
 #include "internal.cuh"
 #include "reduce.cuh"
 
 namespace nekgb {
-
-template <int N>
-struct F32Mat {
-    float d[N * N];   // d[m*N + l] = D(m, l)
-};
 
 struct AxF32Args {
     const float *u;       // MODE 0 input
@@ -31,48 +26,14 @@ struct AxF32Args {
     int64_t E;
 };
 
-__host__ __device__ constexpr int ax_f32_threads(int n) {
-    return n <= 12 ? ((3 * n * n + 31) / 32) * 32 : ((3 * n * n + 1) / 2 + 31) / 32 * 32;
-}
-
-template <int N>
-__device__ __forceinline__ int f32_line_of(int task, int &stride) {
-    constexpr int N2 = N * N;
-    const int d = task / N2;
-    const int c = task - d * N2;
-    const int a0 = c % N, a1 = c / N;
-    if (d == 0) { stride = 1; return N * (a0 + N * a1); }
-    if (d == 1) { stride = N; return a0 + N2 * a1; }
-    stride = N2;
-    return a0 + N * a1;
-}
-
-// Asynchronous global->shared copies (cp.async, no register staging): the
-// element's geometric factors stream into shared memory while the forward
-// derivatives are computed.  16-byte chunks when the slab is 16-byte
-// aligned (n even), 4-byte otherwise.
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
 // MODE 0: w = ax_e(u).  MODE 1: inner CG head (x += x_alpha p, p = r + beta
 // p, w = ax_e(p), box faces zeroed, element-interior <w,p> per CTA).
 template <int N, int MODE>
 __global__ void __launch_bounds__(ax_f32_threads(N))
 ax_f32_kernel(AxF32Args a, const __grid_constant__ F32Mat<N> D) {
-    constexpr int N2 = N * N, N3 = N * N * N;
+    constexpr int N3 = N * N * N;
     constexpr int T = ax_f32_threads(N);
     extern __shared__ __align__(16) float smf[];
-    float *U = smf, *W0 = smf + N3, *W1 = smf + 2 * N3, *W2 = smf + 3 * N3;
-    float *P1 = smf + 4 * N3, *P2 = smf + 5 * N3;
-    float *G = smf + ((6 * N3 + 3) / 4) * 4;   // 6 N3 geometric factors, 16-byte aligned
     __shared__ double red[32];
     float beta = 0.f, xa = 0.f;
     dfa::Acc32 dot;
@@ -81,99 +42,111 @@ ax_f32_kernel(AxF32Args a, const __grid_constant__ F32Mat<N> D) {
         beta = a.sc->it == 0 ? 0.f : (float)a.sc->beta;
         xa = (float)a.sc->x_alpha;
     }
-    const int t = threadIdx.x;
     for (int64_t e = blockIdx.x; e < a.E; e += gridDim.x) {
         const int64_t eb = e * N3;
-        for (int q = t; q < N3; q += T) {
-            float v;
-            if (MODE == 1) {
-                const float pold = a.p[eb + q];
-                if (xa != 0.f) a.x[eb + q] = fmaf(xa, pold, a.x[eb + q]);
-                v = fmaf(beta, pold, a.r[eb + q]);
-                a.p[eb + q] = v;
-            } else {
-                v = __ldg(a.u + eb + q);
-            }
-            U[q] = v;
-        }
-        {   // prefetch this element's gxyz (consumed after the forward phase)
-            const float *gsrc = a.g + e * 6 * N3;
-            if ((N3 % 4) == 0) {
-                for (int q = t; q < 6 * N3 / 4; q += T) cp_async16(G + 4 * q, gsrc + 4 * q);
-            } else {
-                for (int q = t; q < 6 * N3; q += T) cp_async4(G + q, gsrc + q);
-            }
-            cp_async_commit();
-        }
-        __syncthreads();
-        for (int task = t; task < 3 * N2; task += T) {
-            int stride;
-            const int base = f32_line_of<N>(task, stride);
-            float *Wd = task < N2 ? W0 : (task < 2 * N2 ? W1 : W2);
-            float x[N];
-#pragma unroll
-            for (int l = 0; l < N; l++) x[l] = U[base + l * stride];
-#pragma unroll
-            for (int m = 0; m < N; m++) {
-                float acc = D.d[m * N] * x[0];
-#pragma unroll
-                for (int l = 1; l < N; l++) acc = fmaf(D.d[m * N + l], x[l], acc);
-                Wd[base + m * stride] = acc;
-            }
-        }
-        cp_async_wait_all();
-        __syncthreads();
-        for (int q = t; q < N3; q += T) {
-            const float wr = W0[q], ws = W1[q], wt = W2[q];
-            const float g0 = G[q], g1 = G[N3 + q], g2 = G[2 * N3 + q];
-            const float g3 = G[3 * N3 + q], g4 = G[4 * N3 + q], g5 = G[5 * N3 + q];
-            W0[q] = fmaf(g0, wr, fmaf(g1, ws, g2 * wt));
-            W1[q] = fmaf(g1, wr, fmaf(g3, ws, g4 * wt));
-            W2[q] = fmaf(g2, wr, fmaf(g4, ws, g5 * wt));
-        }
-        __syncthreads();
-        for (int task = t; task < 3 * N2; task += T) {
-            int stride;
-            const int base = f32_line_of<N>(task, stride);
-            const float *Ud = task < N2 ? W0 : (task < 2 * N2 ? W1 : W2);
-            float *Pd = task < N2 ? U : (task < 2 * N2 ? P1 : P2);
-            float x[N];
-#pragma unroll
-            for (int l = 0; l < N; l++) x[l] = Ud[base + l * stride];
-#pragma unroll
-            for (int m = 0; m < N; m++) {
-                float acc = D.d[m] * x[0];
-#pragma unroll
-                for (int l = 1; l < N; l++) acc = fmaf(D.d[l * N + m], x[l], acc);
-                Pd[base + m * stride] = acc;
-            }
-        }
-        __syncthreads();
+        F32ElemIO io;
+        io.u = MODE == 0 ? a.u + eb : nullptr;
+        io.r = MODE == 1 ? a.r + eb : nullptr;
+        io.p = MODE == 1 ? a.p + eb : nullptr;
+        io.x = MODE == 1 ? a.x + eb : nullptr;
+        io.w = a.w + eb;
+        io.g = a.g + e * 6 * N3;
         int ex = 0, ey = 0, ez = 0;
         if (MODE == 1) element_coords(e, a.m, ex, ey, ez);
-        for (int q = t; q < N3; q += T) {
-            float wv = U[q] + P1[q] + P2[q];
-            if (MODE == 1) {
-                const int i = q % N, j = (q / N) % N, k = q / N2;
-                if (on_box_face(i, j, k, ex, ey, ez, a.m))
-                    wv = 0.f;
-                else if (i > 0 && i < N - 1 && j > 0 && j < N - 1 && k > 0 && k < N - 1)
-                    dot.add_prod(wv, a.p[eb + q]);
+        f32_element<N, MODE, T>(io, beta, xa, ex, ey, ez, a.m, D, smf, dot);
+    }
+    if (MODE == 1) {
+        const double b = block_sum(dot.value(), red);
+        if (threadIdx.x == 0) a.partials[blockIdx.x] = b;
+    }
+}
+
+// The same operator with bulk-copy staging two elements deep (see
+// f32_element_staged): thread 0 arms the next element's barrier and issues
+// its copies, every thread waits (bounded) for the current one.  A copy
+// that does not complete within ~1 s ends the kernel with NB_ERR_TIMEOUT in
+// the scalar block (err), after draining the copies in flight.
+template <int N, int MODE>
+__global__ void __launch_bounds__(ax_f32_threads(N))
+ax_f32_staged_kernel(AxF32Args a, CgScalars *err, const __grid_constant__ F32Mat<N> D) {
+    constexpr int N3 = N * N * N;
+    constexpr int T = ax_f32_threads(N);
+    constexpr int STAGE = f32_stage_floats<N, MODE>();
+    extern __shared__ __align__(16) float smf[];
+    __shared__ double red[32];
+    __shared__ __align__(8) uint64_t bars[2];
+    float beta = 0.f, xa = 0.f;
+    dfa::Acc32 dot;
+    if (MODE == 1) {
+        if (a.sc->done) return;
+        beta = a.sc->it == 0 ? 0.f : (float)a.sc->beta;
+        xa = (float)a.sc->x_alpha;
+    }
+    const int t = threadIdx.x;
+    if (t == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool with_x = MODE == 1 && xa != 0.f;
+    const unsigned bytes = 4u * (MODE == 1 ? (with_x ? 9 : 8) : 7) * N3;
+    auto issue = [&](int64_t e, int s) {   // thread 0
+        float *st = smf + s * STAGE;
+        mbar_expect_tx(&bars[s], bytes);
+        bulk_g2s(st, a.g + e * 6 * N3, 4u * 6 * N3, &bars[s]);
+        if (MODE == 1) {
+            bulk_g2s(st + 6 * N3, a.r + e * N3, 4u * N3, &bars[s]);
+            bulk_g2s(st + 7 * N3, a.p + e * N3, 4u * N3, &bars[s]);
+            if (with_x) bulk_g2s(st + 8 * N3, a.x + e * N3, 4u * N3, &bars[s]);
+        } else {
+            bulk_g2s(st + 6 * N3, a.u + e * N3, 4u * N3, &bars[s]);
+        }
+    };
+    int issued[2] = {0, 0}, waited[2] = {0, 0};
+    int64_t e = blockIdx.x;
+    if (t == 0 && e < a.E) issue(e, 0);
+    issued[0] = e < a.E ? 1 : 0;
+    bool ok = true;
+    for (int i = 0; e < a.E; e += gridDim.x, i++) {
+        const int s = i & 1;
+        const int64_t en = e + gridDim.x;
+        if (en < a.E) {
+            if (t == 0) issue(en, s ^ 1);
+            issued[s ^ 1]++;
+        }
+        ok = __syncthreads_and(mbar_wait(&bars[s], waited[s] & 1)) != 0;
+        if (!ok) break;
+        waited[s]++;
+        F32StagedOut o;
+        o.p = MODE == 1 ? a.p + e * N3 : nullptr;
+        o.x = MODE == 1 ? a.x + e * N3 : nullptr;
+        o.w = a.w + e * N3;
+        int ex = 0, ey = 0, ez = 0;
+        if (MODE == 1) element_coords(e, a.m, ex, ey, ez);
+        f32_element_staged<N, MODE, T>(smf + s * STAGE, smf + 2 * STAGE, o, beta, xa, ex, ey, ez, a.m, D, dot);
+    }
+    if (!ok) {   // drain the copies in flight before leaving, then report
+        if (t == 0) {
+            for (int s = 0; s < 2; s++)
+                if (issued[s] > waited[s]) mbar_wait(&bars[s], waited[s] & 1);
+            if (err) {
+                err->status = (int)NB_ERR_TIMEOUT;
+                err->done = 1;
             }
-            a.w[eb + q] = wv;
         }
         __syncthreads();
     }
     if (MODE == 1) {
         const double b = block_sum(dot.value(), red);
-        if (t == 0) a.partials[blockIdx.x] = b;
+        if (threadIdx.x == 0) a.partials[blockIdx.x] = b;
     }
 }
 
 template <int N>
 static nb_status launch_f32_n(nb_ctx *c, const float *u, float *w, int mode) {
     constexpr int T = ax_f32_threads(N);
-    const size_t smem = sizeof(float) * (((6 * N * N * N + 3) / 4) * 4 + 6 * N * N * N);
+    const size_t smem = sizeof(float) * f32_smem_floats(N);
     static bool configured[2] = {false, false};
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
@@ -194,6 +167,27 @@ static nb_status launch_f32_n(nb_ctx *c, const float *u, float *w, int mode) {
         args.w = c->d_w32;
         args.sc = c->d_sc;
         args.partials = c->d_partials;
+    }
+    if constexpr (f32_staged_ok<N>()) {
+        if (!c->f32_plain) {
+            auto kern = mode == 0 ? ax_f32_staged_kernel<N, 0> : ax_f32_staged_kernel<N, 1>;
+            const size_t ssm = sizeof(float) * (mode == 0 ? f32_staged_smem_floats<N, 0>()
+                                                          : f32_staged_smem_floats<N, 1>());
+            static bool staged_configured[2] = {false, false};
+            if (!staged_configured[mode]) {
+                NB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+                staged_configured[mode] = true;
+            }
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, ssm);
+            if (occ < 1) occ = 1;
+            const int64_t cap = (int64_t)sms * occ;
+            const int grid = (int)(c->m.E < cap ? c->m.E : cap);
+            if (mode == 1) c->ax_grid = grid;
+            LaunchTimer tm(c, NB_K_AX);
+            kern<<<grid, T, ssm, c->stream>>>(args, c->d_sc, D);
+            NB_LAUNCH_CHECK("ax_f32_staged_kernel");
+            return NB_OK;
+        }
     }
     auto kern = mode == 0 ? ax_f32_kernel<N, 0> : ax_f32_kernel<N, 1>;
     if (!configured[mode]) {

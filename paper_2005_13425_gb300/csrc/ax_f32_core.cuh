@@ -1,0 +1,289 @@
+// FP32 ax_e element operator (Listing 1, arXiv 2005.13425 Sec. III, with
+// FP32 u, w and gxyz) shared by the single-problem kernel (ax_f32.cu) and
+// the batched engine (engine.cu).
+//
+// Line-thread layout: 3n^2 line tasks own one 1-D line each; D entries are
+// compile-time-indexed kernel parameters (constant-bank operands); a
+// pointwise pass contracts with the six geometric factors; the transposed
+// derivatives go to three partial arrays that a final pass adds.  The
+// element's geometric factors stream into shared memory with cp.async while
+// the forward derivatives are computed.
+#pragma once
+
+#include "bulk.cuh"
+#include "df.cuh"
+#include "internal.cuh"
+#include "reduce.cuh"
+
+namespace nekgb {
+
+template <int N>
+struct F32Mat {
+    float d[N * N];   // d[m*N + l] = D(m, l)
+};
+
+__host__ __device__ constexpr int ax_f32_threads(int n) {
+    return n <= 12 ? ((3 * n * n + 31) / 32) * 32 : ((3 * n * n + 1) / 2 + 31) / 32 * 32;
+}
+
+// Floats of dynamic shared memory f32_element needs: six n^3 work arrays and
+// the six n^3 geometric factors (16-byte aligned).
+__host__ __device__ constexpr int f32_smem_floats(int n) {
+    return ((6 * n * n * n + 3) / 4) * 4 + 6 * n * n * n;
+}
+
+template <int N>
+__device__ __forceinline__ int f32_line_of(int task, int &stride) {
+    constexpr int N2 = N * N;
+    const int d = task / N2;
+    const int c = task - d * N2;
+    const int a0 = c % N, a1 = c / N;
+    if (d == 0) { stride = 1; return N * (a0 + N * a1); }
+    if (d == 1) { stride = N; return a0 + N2 * a1; }
+    stride = N2;
+    return a0 + N * a1;
+}
+
+// Asynchronous global->shared copies (no register staging): 16-byte chunks
+// when the element's slab is 16-byte aligned (n^3 a multiple of 4), 4-byte
+// otherwise.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Per-element arguments of f32_element (pointers offset to the element).
+struct F32ElemIO {
+    const float *u;   // MODE 0: input
+    const float *r;   // MODE 1: residual
+    float *p;         // MODE 1: search direction (updated in place)
+    float *x;         // MODE 1: iterate (owed update applied when xa != 0)
+    float *w;         // output
+    const float *g;   // gxyz [6][n^3] of the element
+};
+
+// One element, executed by the whole CTA of T threads (contains barriers;
+// every thread must call it).  MODE 0: w = ax_e(u).  MODE 1: the inner CG
+// head, x += xa p, p = r + beta p, w = ax_e(p) with box-face points zeroed
+// and the element-interior <w,p> added to dot.  (ex, ey, ez) is the
+// element's position in the box m.
+template <int N, int MODE, int T>
+__device__ __forceinline__ void f32_element(const F32ElemIO &io, float beta, float xa, int ex, int ey, int ez,
+                                            const Mesh &m, const F32Mat<N> &D, float *smf, dfa::Acc32 &dot) {
+    constexpr int N2 = N * N, N3 = N * N * N;
+    float *U = smf, *W0 = smf + N3, *W1 = smf + 2 * N3, *W2 = smf + 3 * N3;
+    float *P1 = smf + 4 * N3, *P2 = smf + 5 * N3;
+    float *G = smf + ((6 * N3 + 3) / 4) * 4;
+    const int t = threadIdx.x;
+    if (MODE == 1) {
+        if (xa != 0.f) {
+            for (int q = t; q < N3; q += T) {
+                const float pold = io.p[q];
+                io.x[q] = fmaf(xa, pold, io.x[q]);
+                const float v = fmaf(beta, pold, io.r[q]);
+                io.p[q] = v;
+                U[q] = v;
+            }
+        } else {
+            for (int q = t; q < N3; q += T) {
+                const float v = fmaf(beta, io.p[q], io.r[q]);
+                io.p[q] = v;
+                U[q] = v;
+            }
+        }
+    } else {
+        for (int q = t; q < N3; q += T) U[q] = __ldg(io.u + q);
+    }
+    // prefetch the geometric factors (consumed after the forward phase)
+    if ((N3 % 4) == 0) {
+        for (int q = t; q < 6 * N3 / 4; q += T) cp_async16(G + 4 * q, io.g + 4 * q);
+    } else {
+        for (int q = t; q < 6 * N3; q += T) cp_async4(G + q, io.g + q);
+    }
+    cp_async_commit();
+    __syncthreads();
+    for (int task = t; task < 3 * N2; task += T) {
+        int stride;
+        const int base = f32_line_of<N>(task, stride);
+        float *Wd = task < N2 ? W0 : (task < 2 * N2 ? W1 : W2);
+        float x[N];
+#pragma unroll
+        for (int l = 0; l < N; l++) x[l] = U[base + l * stride];
+#pragma unroll
+        for (int mm = 0; mm < N; mm++) {
+            float acc = D.d[mm * N] * x[0];
+#pragma unroll
+            for (int l = 1; l < N; l++) acc = fmaf(D.d[mm * N + l], x[l], acc);
+            Wd[base + mm * stride] = acc;
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int q = t; q < N3; q += T) {
+        const float wr = W0[q], ws = W1[q], wt = W2[q];
+        const float g0 = G[q], g1 = G[N3 + q], g2 = G[2 * N3 + q];
+        const float g3 = G[3 * N3 + q], g4 = G[4 * N3 + q], g5 = G[5 * N3 + q];
+        W0[q] = fmaf(g0, wr, fmaf(g1, ws, g2 * wt));
+        W1[q] = fmaf(g1, wr, fmaf(g3, ws, g4 * wt));
+        W2[q] = fmaf(g2, wr, fmaf(g4, ws, g5 * wt));
+    }
+    __syncthreads();
+    for (int task = t; task < 3 * N2; task += T) {
+        int stride;
+        const int base = f32_line_of<N>(task, stride);
+        const float *Ud = task < N2 ? W0 : (task < 2 * N2 ? W1 : W2);
+        float *Pd = task < N2 ? U : (task < 2 * N2 ? P1 : P2);
+        float x[N];
+#pragma unroll
+        for (int l = 0; l < N; l++) x[l] = Ud[base + l * stride];
+#pragma unroll
+        for (int mm = 0; mm < N; mm++) {
+            float acc = D.d[mm] * x[0];
+#pragma unroll
+            for (int l = 1; l < N; l++) acc = fmaf(D.d[l * N + mm], x[l], acc);
+            Pd[base + mm * stride] = acc;
+        }
+    }
+    __syncthreads();
+    for (int q = t; q < N3; q += T) {
+        float wv = U[q] + P1[q] + P2[q];
+        if (MODE == 1) {
+            const int i = q % N, j = (q / N) % N, k = q / N2;
+            if (on_box_face(i, j, k, ex, ey, ez, m))
+                wv = 0.f;
+            else if (i > 0 && i < N - 1 && j > 0 && j < N - 1 && k > 0 && k < N - 1)
+                dot.add_prod(wv, io.p[q]);
+        }
+        io.w[q] = wv;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- staged
+// The same element operator with every input of an element staged in
+// shared memory by bulk copies (bulk.cuh), two stages deep: while a CTA
+// computes one element, the copy engine fetches the next one's geometric
+// factors and vectors, so the loads of a whole element are always in
+// flight.  Used for even n up to 10 (n^3 a multiple of 4, so every
+// per-element slab is 16-byte aligned, and two CTAs of 21 n^3 floats fit
+// on an SM).
+//
+// Shared memory (floats): stage s at s*f32_stage_floats: G [6n^3] then the
+// vectors (MODE 1: r, p, z; MODE 0: u); after both stages, W0..W2 [3n^3].
+// The backward partials reuse the current stage's G (consumed by then).
+template <int N, int MODE>
+__host__ __device__ constexpr int f32_stage_floats() {
+    return (MODE == 1 ? 9 : 7) * N * N * N;
+}
+template <int N, int MODE>
+__host__ __device__ constexpr int f32_staged_smem_floats() {
+    return 2 * f32_stage_floats<N, MODE>() + 3 * N * N * N;
+}
+template <int N>
+__host__ __device__ constexpr bool f32_staged_ok() {
+    return (N % 2 == 0) && N <= 10;
+}
+
+// Global outputs of one staged element (offset to the element).
+struct F32StagedOut {
+    float *p;   // MODE 1: p = r + beta p written back
+    float *x;   // MODE 1: x += xa p_old written back (when xa != 0)
+    float *w;   // ax_e output
+};
+
+// Element body on stage `st` (whole CTA).  Ends with fence + barrier, after
+// which the stage may be refilled.
+template <int N, int MODE, int T>
+__device__ __forceinline__ void f32_element_staged(float *st, float *W, const F32StagedOut &o, float beta,
+                                                   float xa, int ex, int ey, int ez, const Mesh &m,
+                                                   const F32Mat<N> &D, dfa::Acc32 &dot) {
+    constexpr int N2 = N * N, N3 = N * N * N;
+    float *G = st;
+    float *U = st + 6 * N3;                    // MODE 0: u; MODE 1: r then (below) p
+    float *W0 = W, *W1 = W + N3, *W2 = W + 2 * N3;
+    const int t = threadIdx.x;
+    if (MODE == 1) {
+        float *R = st + 6 * N3, *P = st + 7 * N3, *Z = st + 8 * N3;
+        if (xa != 0.f) {
+            for (int q = t; q < N3; q += T) {
+                const float pold = P[q];
+                const float pn = fmaf(beta, pold, R[q]);
+                P[q] = pn;
+                o.p[q] = pn;
+                o.x[q] = fmaf(xa, pold, Z[q]);
+            }
+        } else {
+            for (int q = t; q < N3; q += T) {
+                const float pn = fmaf(beta, P[q], R[q]);
+                P[q] = pn;
+                o.p[q] = pn;
+            }
+        }
+        U = P;
+        __syncthreads();
+    }
+    for (int task = t; task < 3 * N2; task += T) {
+        int stride;
+        const int base = f32_line_of<N>(task, stride);
+        float *Wd = task < N2 ? W0 : (task < 2 * N2 ? W1 : W2);
+        float x[N];
+#pragma unroll
+        for (int l = 0; l < N; l++) x[l] = U[base + l * stride];
+#pragma unroll
+        for (int mm = 0; mm < N; mm++) {
+            float acc = D.d[mm * N] * x[0];
+#pragma unroll
+            for (int l = 1; l < N; l++) acc = fmaf(D.d[mm * N + l], x[l], acc);
+            Wd[base + mm * stride] = acc;
+        }
+    }
+    __syncthreads();
+    for (int q = t; q < N3; q += T) {
+        const float wr = W0[q], ws = W1[q], wt = W2[q];
+        const float g0 = G[q], g1 = G[N3 + q], g2 = G[2 * N3 + q];
+        const float g3 = G[3 * N3 + q], g4 = G[4 * N3 + q], g5 = G[5 * N3 + q];
+        W0[q] = fmaf(g0, wr, fmaf(g1, ws, g2 * wt));
+        W1[q] = fmaf(g1, wr, fmaf(g3, ws, g4 * wt));
+        W2[q] = fmaf(g2, wr, fmaf(g4, ws, g5 * wt));
+    }
+    __syncthreads();
+    float *P0 = G, *P1 = G + N3, *P2 = G + 2 * N3;   // G is consumed
+    for (int task = t; task < 3 * N2; task += T) {
+        int stride;
+        const int base = f32_line_of<N>(task, stride);
+        const float *Ud = task < N2 ? W0 : (task < 2 * N2 ? W1 : W2);
+        float *Pd = task < N2 ? P0 : (task < 2 * N2 ? P1 : P2);
+        float x[N];
+#pragma unroll
+        for (int l = 0; l < N; l++) x[l] = Ud[base + l * stride];
+#pragma unroll
+        for (int mm = 0; mm < N; mm++) {
+            float acc = D.d[mm] * x[0];
+#pragma unroll
+            for (int l = 1; l < N; l++) acc = fmaf(D.d[l * N + mm], x[l], acc);
+            Pd[base + mm * stride] = acc;
+        }
+    }
+    __syncthreads();
+    for (int q = t; q < N3; q += T) {
+        float wv = P0[q] + P1[q] + P2[q];
+        if (MODE == 1) {
+            const int i = q % N, j = (q / N) % N, k = q / N2;
+            if (on_box_face(i, j, k, ex, ey, ez, m))
+                wv = 0.f;
+            else if (i > 0 && i < N - 1 && j > 0 && j < N - 1 && k > 0 && k < N - 1)
+                dot.add_prod(wv, U[q]);
+        }
+        o.w[q] = wv;
+    }
+    fence_proxy_async();
+    __syncthreads();
+}
+
+}  // namespace nekgb

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "ax_df_core.cuh"
+#include "ax_f32_core.cuh"
 #include "gs_nodes.cuh"
 #include "internal.cuh"
 #include "reduce.cuh"
@@ -39,15 +40,30 @@ constexpr int kEngMaxSlots = 1024;
 constexpr int kDsTile = 2048;   // shared nodes per dssum tile (256 threads x 8)
 constexpr int kEngThreads = 256;
 
+// Mixed-precision request phases (defect correction, as in mixed.cu).
+constexpr int kPhaseInner = 0;   // FP32 inner CG iterating
+constexpr int kPhaseOuter = 1;   // FP64 residual step due
+constexpr int kPhaseDone = 2;
+
 struct ProbDesc {
     Mesh m;
     float2 *g;                  // gxyz pairs [E][6][n^3]
-    double *r, *p, *w, *x;      // CG vectors, local storage
-    double *partials;           // ntile_ax + ntile_ds slots
+    double *r, *p, *w, *x;      // CG vectors, local storage (mixed: r, p unused)
+    double *partials;           // FP64: ntile_ax + ntile_ds slots; mixed: 2 ntile_ax + ntile_ds
     int ntile_ax, ntile_ds, te;
     int cx, cy, cz;
-    int pad;
+    int prec;                   // NB_FP64 or NB_MIXED
+    // FP64: sc is the CG state.  Mixed: sc holds the outer state (rr =
+    // <r,r>_c of the FP64 residual, fnorm2, tol, maxit = inner-iteration
+    // budget, it = inner iterations so far, done, status) and si the inner
+    // FP32 CG's scalars.
     CgScalars sc;
+    CgScalars si;
+    int phase, outer, max_outer, pad;
+    double inner_tol;
+    double *f;                  // mixed: right-hand side (FP64, masked)
+    float *g32;                 // mixed: gxyz FP32 [E][6][n^3]
+    float *r32, *p32, *w32, *z32;
 };
 
 // ---------------------------------------------------------------- kernels
@@ -227,6 +243,7 @@ eng_update(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const in
                 P.sc.ticket = 0;
                 P.sc.rho_old = P.sc.rho;
                 P.sc.rho = rho;
+                P.sc.rr = rho;
                 P.sc.beta = rho / P.sc.rho_old;
                 const int it = P.sc.it + 1;
                 P.sc.it = it;
@@ -278,6 +295,7 @@ __global__ void __launch_bounds__(kEngThreads) eng_start(ProbDesc *__restrict__ 
     if (threadIdx.x == 0) {
         P.sc.ticket = 0;
         P.sc.rho = rho;
+        P.sc.rr = rho;
         P.sc.rho_old = 1.0;
         P.sc.fnorm2 = rho;
         P.sc.beta = 0.0;
@@ -291,7 +309,8 @@ __global__ void __launch_bounds__(kEngThreads) eng_start(ProbDesc *__restrict__ 
 // r = mask(Q fu): a field given per unique node (x fastest) copied to every
 // local copy, zero on the faces of the box (the right-hand side of a request
 // submitted in unique-node form).
-__global__ void eng_scatter_mask(ProbDesc *__restrict__ desc, int slot, const double *__restrict__ fu) {
+__global__ void eng_scatter_mask(ProbDesc *__restrict__ desc, int slot, const double *__restrict__ fu,
+                                 double *__restrict__ dst) {
     const ProbDesc &P = desc[slot];
     const Mesh m = P.m;
     const int n = m.n;
@@ -305,7 +324,7 @@ __global__ void eng_scatter_mask(ProbDesc *__restrict__ desc, int slot, const do
         element_coords(e, m, ex, ey, ez);
         const int64_t gx = (int64_t)ex * (n - 1) + i, gy = (int64_t)ey * (n - 1) + j,
                       gz = (int64_t)ez * (n - 1) + k;
-        P.r[q] = on_box_face(i, j, k, ex, ey, ez, m) ? 0.0 : fu[gx + m.NX * (gy + m.NY * gz)];
+        dst[q] = on_box_face(i, j, k, ex, ey, ez, m) ? 0.0 : fu[gx + m.NX * (gy + m.NY * gz)];
     }
 }
 
@@ -317,6 +336,361 @@ __global__ void eng_final_x(ProbDesc *__restrict__ desc, int slot) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P.m.npts;
          q += (int64_t)gridDim.x * blockDim.x)
         P.x[q] = fma(xa, P.p[q], P.x[q]);
+}
+
+// ---------------------------------------------------------------- mixed
+// Mixed-precision requests: defect correction with an FP32 inner CG, as in
+// mixed.cu, driven per problem on the device.  Each engine step first runs
+// the outer pass for the problems whose inner solve ended (x += d, the FP64
+// residual r = f - A x with the FP64-accurate operator, the convergence
+// test and the start of the next inner solve), then the inner iterations.
+// A problem's phase decides which kernels touch it; every decision is taken
+// by the problem's own last tile, so results stay independent of the mix.
+
+// Inner CG head over (slot, tile) work units: z += xa p, p = r + beta p,
+// w = ax_e(p) in FP32, box faces zeroed, element-interior <w,p>_c.
+template <int N, int T>
+__global__ void __launch_bounds__(T)
+eng_m_head(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles,
+           const __grid_constant__ F32Mat<N> D) {
+    constexpr int N3 = N * N * N;
+    extern __shared__ __align__(16) float smf[];
+    __shared__ double red[32];
+    const int nt = *ntiles;
+    for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+        const int2 tile = tiles[ti];
+        ProbDesc &P = desc[tile.x];
+        if (P.phase != kPhaseInner || P.si.done) continue;     // uniform over the CTA
+        const float beta = P.si.it == 0 ? 0.f : (float)P.si.beta;
+        const float xa = (float)P.si.x_alpha;
+        const Mesh m = P.m;
+        const int64_t e0 = (int64_t)tile.y * P.te;
+        const int64_t e1 = e0 + P.te < m.E ? e0 + P.te : m.E;
+        dfa::Acc32 dot;
+        for (int64_t e = e0; e < e1; e++) {
+            const int64_t eb = e * N3;
+            F32ElemIO io;
+            io.u = nullptr;
+            io.r = P.r32 + eb;
+            io.p = P.p32 + eb;
+            io.x = P.z32 + eb;
+            io.w = P.w32 + eb;
+            io.g = P.g32 + e * 6 * N3;
+            int ex, ey, ez;
+            element_coords(e, m, ex, ey, ez);
+            f32_element<N, 1, T>(io, beta, xa, ex, ey, ez, m, D, smf, dot);
+        }
+        const double b = block_sum(dot.value(), red);
+        if (threadIdx.x == 0) P.partials[tile.y] = b;
+    }
+}
+
+// Shared-node sums of the FP32 w (and of the FP64 w in the outer pass, DOT
+// = false) over (slot, node tile) work units.  With DOT, the shared-node
+// <w,p>_c is accumulated and the problem's last tile forms alpha.
+template <typename T, bool DOT>
+__global__ void __launch_bounds__(kEngThreads)
+eng_m_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles) {
+    __shared__ double red[32];
+    __shared__ int s_last;
+    const int nt = *ntiles;
+    for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+        const int2 tile = tiles[ti];
+        ProbDesc &P = desc[tile.x];
+        if (DOT) {
+            if (P.phase != kPhaseInner || P.si.done) continue;
+        } else {
+            if (P.phase != kPhaseOuter || P.outer == 0) continue;   // x = 0 on the first pass: A x = 0
+        }
+        const Mesh m = P.m;
+        const int total = P.cx + P.cy + P.cz;
+        T *w;
+        const float *p = P.p32;
+        if constexpr (DOT) w = P.w32;
+        else w = P.w;
+        dfa::Acc32 dot;
+        const int q0 = tile.y * kDsTile;
+        const int q1 = q0 + kDsTile < total ? q0 + kDsTile : total;
+        for (int q = q0 + threadIdx.x; q < q1; q += kEngThreads) {
+            int gx, gy, gz;
+            shared_node(q, m, P.cx, P.cy, gx, gy, gz);
+            int64_t idx[8];
+            const int c = node_copies(gx, gy, gz, m, idx);
+            T s;
+            if (c == 2) {
+                s = plus_zero(w[idx[0]]) + w[idx[1]];
+            } else if (c == 4) {
+                T a[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) a[k] = w[idx[k]];
+                s = plus_zero(a[0]);
+#pragma unroll
+                for (int k = 1; k < 4; k++) s = s + a[k];
+            } else {
+                T a[8];
+#pragma unroll
+                for (int k = 0; k < 8; k++) a[k] = w[idx[k]];
+                s = plus_zero(a[0]);
+#pragma unroll
+                for (int k = 1; k < 8; k++) s = s + a[k];
+            }
+            for (int k = 0; k < c; k++) w[idx[k]] = s;
+            if constexpr (DOT) {
+                const float sc = s * (c == 2 ? 0.5f : (c == 4 ? 0.25f : 0.125f));
+                for (int k = 0; k < c; k++) dot.add_prod(sc, p[idx[k]]);
+            }
+        }
+        if constexpr (DOT) {
+            const double b = block_sum(dot.value(), red);
+            if (threadIdx.x == 0) {
+                P.partials[P.ntile_ax + tile.y] = b;
+                __threadfence();
+                const unsigned t = atomicAdd(&P.si.ticket, 1u);
+                s_last = (t == (unsigned)P.ntile_ds - 1);
+            }
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                double acc = 0.0;
+                const int cnt = P.ntile_ax + P.ntile_ds;
+                for (int k = threadIdx.x; k < cnt; k += kEngThreads) acc += __ldcg(P.partials + k);
+                const double pap = block_sum(acc, red);
+                if (threadIdx.x == 0) {
+                    P.si.ticket = 0;
+                    P.si.pap = pap;
+                    if (!(pap > 0.0) || !isfinite(pap)) {   // inner breakdown: back to the outer step
+                        P.si.status = (int)NB_ERR_BREAKDOWN;
+                        P.si.done = 1;
+                        P.si.x_alpha = 0.0;
+                        P.phase = kPhaseOuter;
+                    } else {
+                        P.si.alpha = P.si.rho / pap;
+                        P.si.x_alpha = P.si.alpha;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Inner update: r -= alpha w (FP32), rho = <r,r>_c (compensated), beta and
+// the inner convergence test; a finished inner solve hands the problem to
+// the outer step.
+template <int N>
+__global__ void __launch_bounds__(kEngThreads)
+eng_m_update(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles) {
+    constexpr int N3 = N * N * N;
+    __shared__ double red[32];
+    __shared__ int s_last;
+    const int nt = *ntiles;
+    for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+        const int2 tile = tiles[ti];
+        ProbDesc &P = desc[tile.x];
+        if (P.phase != kPhaseInner || P.si.done) continue;
+        const Mesh m = P.m;
+        const float alpha = (float)P.si.alpha;
+        const int64_t e0 = (int64_t)tile.y * P.te;
+        const int64_t e1 = e0 + P.te < m.E ? e0 + P.te : m.E;
+        dfa::Acc32 acc;
+        for (int64_t e = e0; e < e1; e++) {
+            int ex, ey, ez;
+            element_coords(e, m, ex, ey, ez);
+            float *r = P.r32 + e * N3;
+            const float *w = P.w32 + e * N3;
+#pragma unroll 4
+            for (int q = threadIdx.x; q < N3; q += kEngThreads) {
+                const int i = q % N, j = (q / N) % N, k = q / (N * N);
+                const float rn = fmaf(-alpha, w[q], r[q]);
+                r[q] = rn;
+                const float cw = __uint_as_float((unsigned)(127 - log2_mult(i, j, k, ex, ey, ez, m)) << 23);
+                acc.add_prod(rn * cw, rn);
+            }
+        }
+        const double b = block_sum(acc.value(), red);
+        if (threadIdx.x == 0) {
+            P.partials[tile.y] = b;
+            __threadfence();
+            const unsigned t = atomicAdd(&P.si.ticket, 1u);
+            s_last = (t == (unsigned)P.ntile_ax - 1);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            double a2 = 0.0;
+            for (int k = threadIdx.x; k < P.ntile_ax; k += kEngThreads) a2 += __ldcg(P.partials + k);
+            const double rho = block_sum(a2, red);
+            if (threadIdx.x == 0) {
+                P.si.ticket = 0;
+                P.si.rho_old = P.si.rho;
+                P.si.rho = rho;
+                P.si.beta = rho / P.si.rho_old;
+                const int it = P.si.it + 1;
+                P.si.it = it;
+                P.sc.it += 1;
+                const bool conv = sqrt(rho) / sqrt(P.si.fnorm2) <= P.si.tol;
+                if (rho == 0.0 || conv || it >= P.si.maxit) {
+                    P.si.done = 1;
+                    P.phase = kPhaseOuter;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Outer step, part 1: x += d, with d = z + x_alpha p (the inner solve's
+// owed update), in FP64.  Skipped on the first pass (x = 0, no inner solve).
+template <int N>
+__global__ void __launch_bounds__(kEngThreads)
+eng_m_outer_x(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles) {
+    constexpr int N3 = N * N * N;
+    const int nt = *ntiles;
+    for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+        const int2 tile = tiles[ti];
+        const ProbDesc &P = desc[tile.x];
+        if (P.phase != kPhaseOuter || P.outer == 0) continue;
+        const float xa = (float)P.si.x_alpha;
+        const int64_t q0 = (int64_t)tile.y * P.te * N3;
+        const int64_t q1 = (int64_t)(tile.y + 1) * P.te * N3 < P.m.npts ? (int64_t)(tile.y + 1) * P.te * N3
+                                                                          : P.m.npts;
+        for (int64_t q = q0 + threadIdx.x; q < q1; q += kEngThreads) {
+            const float d = fmaf(xa, P.p32[q], P.z32[q]);
+            P.x[q] += (double)d;
+        }
+    }
+}
+
+// Outer step, part 2: w = ax_e(x) with the FP64-accurate (double-float)
+// element operator.  Skipped on the first pass.
+template <int N, int T>
+__global__ void __launch_bounds__(T)
+eng_m_outer_ax(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles,
+               const __grid_constant__ DfEo<N> D) {
+    constexpr int N3 = N * N * N;
+    extern __shared__ float2 sm[];
+    __shared__ int s_emax;
+    if (threadIdx.x == 0) s_emax = 0;
+    __syncthreads();
+    const int nt = *ntiles;
+    for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+        const int2 tile = tiles[ti];
+        const ProbDesc &P = desc[tile.x];
+        if (P.phase != kPhaseOuter || P.outer == 0) continue;
+        const Mesh m = P.m;
+        const int64_t e0 = (int64_t)tile.y * P.te;
+        const int64_t e1 = e0 + P.te < m.E ? e0 + P.te : m.E;
+        double dot = 0.0;
+        for (int64_t e = e0; e < e1; e++) {
+            const int64_t eb = e * N3;
+            DfElemIO io;
+            io.u = P.x + eb;
+            io.r = nullptr;
+            io.p = nullptr;
+            io.x = nullptr;
+            io.minv = nullptr;
+            io.w = P.w + eb;
+            io.g = P.g + e * 6 * N3;
+            df_element<N, 0, true, T>(io, 0.0, 0.0, false, 1023, m, 0, 0, 0, D, sm, &s_emax, dot);
+        }
+    }
+}
+
+// Outer step, part 3: r = mask(f - w) (w = A x after dssum; A x = 0 on the
+// first pass), rr = <r,r>_c in FP64, and the inner right-hand side
+// r32 = fl32(r) with p32 = z32 = 0 and rho32 = <r32,r32>_c.  The problem's
+// last tile decides: converged (or out of budget) -> done; otherwise the
+// next inner solve starts.
+template <int N>
+__global__ void __launch_bounds__(kEngThreads)
+eng_m_outer_resid(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles) {
+    constexpr int N3 = N * N * N;
+    __shared__ double red[32];
+    __shared__ int s_last;
+    const int nt = *ntiles;
+    for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+        const int2 tile = tiles[ti];
+        ProbDesc &P = desc[tile.x];
+        if (P.phase != kPhaseOuter) continue;
+        const Mesh m = P.m;
+        const bool first = P.outer == 0;
+        const int64_t e0 = (int64_t)tile.y * P.te;
+        const int64_t e1 = e0 + P.te < m.E ? e0 + P.te : m.E;
+        double acc = 0.0;
+        dfa::Acc32 acc32;
+        for (int64_t e = e0; e < e1; e++) {
+            int ex, ey, ez;
+            element_coords(e, m, ex, ey, ez);
+            const int64_t eb = e * N3;
+            for (int q = threadIdx.x; q < N3; q += kEngThreads) {
+                const int i = q % N, j = (q / N) % N, k = q / (N * N);
+                double rv = 0.0;
+                if (!on_box_face(i, j, k, ex, ey, ez, m)) rv = first ? P.f[eb + q] : P.f[eb + q] - P.w[eb + q];
+                const int lg = log2_mult(i, j, k, ex, ey, ez, m);
+                acc = fma(scale_down_pow2(rv, lg), rv, acc);
+                const float r32 = __double2float_rn(rv);
+                P.r32[eb + q] = r32;
+                P.p32[eb + q] = 0.f;
+                P.z32[eb + q] = 0.f;
+                acc32.add_prod(r32 * __uint_as_float((unsigned)(127 - lg) << 23), r32);
+            }
+        }
+        const double b = block_sum(acc, red);
+        const double b32 = block_sum(acc32.value(), red);
+        if (threadIdx.x == 0) {
+            P.partials[tile.y] = b;
+            P.partials[P.ntile_ax + P.ntile_ds + tile.y] = b32;
+            __threadfence();
+            const unsigned t = atomicAdd(&P.sc.ticket, 1u);
+            s_last = (t == (unsigned)P.ntile_ax - 1);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            double a2 = 0.0, a3 = 0.0;
+            for (int k = threadIdx.x; k < P.ntile_ax; k += kEngThreads) {
+                a2 += __ldcg(P.partials + k);
+                a3 += __ldcg(P.partials + P.ntile_ax + P.ntile_ds + k);
+            }
+            const double rr = block_sum(a2, red);
+            const double rho32 = block_sum(a3, red);
+            if (threadIdx.x == 0) {
+                P.sc.ticket = 0;
+                P.sc.rr = rr;
+                P.sc.rho = rr;
+                if (first) P.sc.fnorm2 = rr;
+                const bool conv = rr == 0.0 || (P.sc.tol > 0.0 && sqrt(rr) / sqrt(P.sc.fnorm2) <= P.sc.tol);
+                if (conv || P.outer >= P.max_outer || P.sc.it >= P.sc.maxit) {
+                    P.phase = kPhaseDone;
+                    P.sc.done = 1;
+                } else {
+                    CgScalars &si = P.si;
+                    si.rho = rho32;
+                    si.rr = rho32;
+                    si.rho_old = 1.0;
+                    si.fnorm2 = rho32;
+                    si.beta = 0.0;
+                    si.alpha = 0.0;
+                    si.x_alpha = 0.0;
+                    si.it = 0;
+                    si.status = 0;
+                    si.tol = P.inner_tol;
+                    si.maxit = P.sc.maxit - P.sc.it;
+                    si.done = rho32 == 0.0 ? 1 : 0;
+                    P.outer += 1;
+                    P.phase = si.done ? kPhaseOuter : kPhaseInner;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// FP32 geometric factors of a mixed request from its pairs (h + l): h.
+__global__ void eng_pairs_to_f32(const float2 *__restrict__ g, float *__restrict__ g32, int64_t n) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x)
+        g32[q] = g[q].x;
 }
 
 }  // namespace nekgb
@@ -367,6 +741,7 @@ struct Arena {
 struct EngSlot {
     bool used = false;
     int n = 0;
+    int prec = 0;
     size_t off = 0, bytes = 0;
     double t_submit = 0.0;
 };
@@ -388,25 +763,32 @@ struct nb_engine {
     nekgb::Arena arena;
     nekgb::ProbDesc *d_desc = nullptr, *h_desc = nullptr;
     nekgb::EngSlot slots[nekgb::kEngMaxSlots];
-    nekgb::NGroup groups[nekgb::kMaxN + 1];
+    nekgb::NGroup groups[nekgb::kMaxN + 1];    // FP64 requests, per n
+    nekgb::NGroup mgroups[nekgb::kMaxN + 1];   // mixed-precision requests, per n
     cudaGraphExec_t graph = nullptr;
-    unsigned graph_key = 0;
+    unsigned long long graph_key = 0;
     int graph_chunk = 0;
     int sms = 1;
 };
 
 namespace nekgb {
 
-static size_t desc_footprint(const Mesh &m, int te, size_t *parts) {
+// Arena bytes of one request.  FP64: gxyz pairs, four CG vectors (r, p, w,
+// x) and the tile partials.  Mixed: gxyz pairs and FP32 gxyz, three FP64
+// vectors (f, w, x), four FP32 vectors (r, p, w, z) and the partials.
+static size_t desc_footprint(const Mesh &m, int prec, size_t *parts) {
     const int64_t n3 = (int64_t)m.n * m.n * m.n;
     int cx, cy, cz;
     shared_counts(m, cx, cy, cz);
-    const int64_t ntax = (m.E + te - 1) / te;
+    const int64_t ntax = (m.E + 3) / 4;   // partial slots for the smallest tile (4 elements)
     const int64_t total = (int64_t)cx + cy + cz;
     const int64_t ntds = total > 0 ? (total + kDsTile - 1) / kDsTile : 1;
     parts[0] = Arena::align(sizeof(float2) * 6 * n3 * m.E);          // gxyz pairs
-    parts[1] = Arena::align(sizeof(double) * m.npts);                 // each CG vector
-    parts[2] = Arena::align(sizeof(double) * (ntax + ntds + 1));      // partials
+    parts[1] = Arena::align(sizeof(double) * m.npts);                 // each FP64 vector
+    parts[2] = Arena::align(sizeof(double) * (2 * ntax + ntds + 1));  // partials
+    parts[3] = Arena::align(sizeof(float) * 6 * n3 * m.E);            // FP32 gxyz
+    parts[4] = Arena::align(sizeof(float) * m.npts);                  // each FP32 vector
+    if (prec == NB_MIXED) return parts[0] + 3 * parts[1] + parts[2] + parts[3] + 4 * parts[4];
     return parts[0] + 4 * parts[1] + parts[2];
 }
 
@@ -480,6 +862,69 @@ static nb_status dispatch_start(nb_engine *g, int n, int slot, int grid) {
     return NB_OK;
 }
 
+// ---- mixed-precision groups
+template <int N>
+static nb_status mixed_inner_iteration(nb_engine *g, const NGroup &G) {
+    constexpr int T = ax_f32_threads(N);
+    const size_t smem = sizeof(float) * f32_smem_floats(N);
+    static bool configured = false;
+    if (!configured) {
+        NB_CUDA(cudaFuncSetAttribute(eng_m_head<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = true;
+    }
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, eng_m_head<N, T>, T, smem);
+    if (occ < 1) occ = 1;
+    F32Mat<N> D;
+    for (int q = 0; q < N * N; q++) D.d[q] = (float)G.D[q];
+    eng_m_head<N, T><<<g->sms * occ, T, smem, g->stream>>>(g->d_desc, G.d_ax, G.d_cnt, D);
+    NB_LAUNCH_CHECK("eng_m_head");
+    eng_m_dssum<float, true><<<g->sms * 8, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ds, G.d_cnt + 1);
+    NB_LAUNCH_CHECK("eng_m_dssum");
+    eng_m_update<N><<<g->sms * 4, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ax, G.d_cnt);
+    NB_LAUNCH_CHECK("eng_m_update");
+    return NB_OK;
+}
+
+template <int N>
+static nb_status mixed_outer_pass(nb_engine *g, const NGroup &G) {
+    constexpr int T = ax_df_threads(N);
+    const size_t smem = sizeof(float2) * 6 * N * N * N;
+    static bool configured = false;
+    if (!configured) {
+        NB_CUDA(cudaFuncSetAttribute(eng_m_outer_ax<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = true;
+    }
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, eng_m_outer_ax<N, T>, T, smem);
+    if (occ < 1) occ = 1;
+    DfEo<N> D;
+    eo_consts<N>(G.D, false, D.fwd);
+    eo_consts<N>(G.D, true, D.bwd);
+    eng_m_outer_x<N><<<g->sms * 4, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ax, G.d_cnt);
+    NB_LAUNCH_CHECK("eng_m_outer_x");
+    eng_m_outer_ax<N, T><<<g->sms * occ, T, smem, g->stream>>>(g->d_desc, G.d_ax, G.d_cnt, D);
+    NB_LAUNCH_CHECK("eng_m_outer_ax");
+    eng_m_dssum<double, false><<<g->sms * 8, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ds, G.d_cnt + 1);
+    NB_LAUNCH_CHECK("eng_m_dssum (outer)");
+    eng_m_outer_resid<N><<<g->sms * 4, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ax, G.d_cnt);
+    NB_LAUNCH_CHECK("eng_m_outer_resid");
+    return NB_OK;
+}
+
+static nb_status dispatch_mixed(nb_engine *g, int n, bool outer) {
+    const NGroup &G = g->mgroups[n];
+    switch (n) {
+#define NB_CASE(NN) \
+    case NN: return outer ? mixed_outer_pass<NN>(g, G) : mixed_inner_iteration<NN>(g, G);
+        NB_CASE(2) NB_CASE(3) NB_CASE(4) NB_CASE(5) NB_CASE(6) NB_CASE(7) NB_CASE(8)
+        NB_CASE(9) NB_CASE(10) NB_CASE(11) NB_CASE(12) NB_CASE(13) NB_CASE(14) NB_CASE(15)
+        NB_CASE(16)
+#undef NB_CASE
+    }
+    return fail(NB_ERR_ARG, "unsupported n");
+}
+
 // ---- autotuner: lines per thread and elements per tile, per n
 static std::mutex g_tune_mu;
 
@@ -513,7 +958,7 @@ static void tune_store(const std::string &key, int lpt, int te) {
 
 nb_status engine_submit_internal(nb_engine *g, nb_box box, int n, double amp, const double *s3,
                                  double tol, int maxit, const double *f, int te, int *id,
-                                 bool f_unique = false);
+                                 bool f_unique = false, int prec = NB_FP64, double inner_tol = 0.0);
 nb_status engine_retire_internal(nb_engine *g, int id, double *x);
 nb_status engine_step_internal(nb_engine *g, int iters);
 
@@ -602,8 +1047,7 @@ static nb_status autotune(nb_engine *g, int n) {
     return st;
 }
 
-static nb_status ensure_group(nb_engine *g, int n, int64_t max_tiles_ax, int64_t max_tiles_ds) {
-    NGroup &G = g->groups[n];
+static nb_status ensure_group(nb_engine *g, NGroup &G, int n, int64_t max_tiles_ax, int64_t max_tiles_ds) {
     if (!G.d_cnt) {
         double xi[kMaxN], w[kMaxN];
         nb_status s = host_gll(n, xi, w);
@@ -639,8 +1083,9 @@ static nb_status ensure_group(nb_engine *g, int n, int64_t max_tiles_ax, int64_t
 
 // Rebuild the device tile lists of the groups whose membership changed.
 static nb_status refresh_tiles(nb_engine *g) {
-    for (int n = 2; n <= kMaxN; n++) {
-        NGroup &G = g->groups[n];
+    for (int gi = 0; gi < 2 * (kMaxN + 1); gi++) {
+        const int n = gi % (kMaxN + 1);
+        NGroup &G = gi <= kMaxN ? g->groups[n] : g->mgroups[n];
         if (!G.dirty) continue;
         std::vector<int2> ax, ds;
         for (int slot : G.slots) {
@@ -648,7 +1093,7 @@ static nb_status refresh_tiles(nb_engine *g) {
             for (int j = 0; j < P.ntile_ax; j++) ax.push_back(make_int2(slot, j));
             for (int j = 0; j < P.ntile_ds; j++) ds.push_back(make_int2(slot, j));
         }
-        nb_status s = ensure_group(g, n, (int64_t)ax.size(), (int64_t)ds.size());
+        nb_status s = ensure_group(g, G, n, (int64_t)ax.size(), (int64_t)ds.size());
         if (s != NB_OK) return s;
         if (!ax.empty())
             NB_CUDA(cudaMemcpyAsync(G.d_ax, ax.data(), sizeof(int2) * ax.size(), cudaMemcpyHostToDevice, g->stream));
@@ -664,10 +1109,11 @@ static nb_status refresh_tiles(nb_engine *g) {
 
 nb_status engine_submit_internal(nb_engine *g, nb_box box, int n, double amp, const double *s3,
                                  double tol, int maxit, const double *f, int te, int *id,
-                                 bool f_unique) {
+                                 bool f_unique, int prec, double inner_tol) {
     const Mesh m = make_mesh(box, n);
-    size_t parts[3];
-    const size_t bytes = desc_footprint(m, te, parts);
+    const bool mixed = prec == NB_MIXED;
+    size_t parts[5];
+    const size_t bytes = desc_footprint(m, prec, parts);
     int slot = -1;
     for (int k = 0; k < kEngMaxSlots; k++)
         if (!g->slots[k].used) { slot = k; break; }
@@ -676,18 +1122,35 @@ nb_status engine_submit_internal(nb_engine *g, nb_box box, int n, double amp, co
     if (!g->arena.alloc(bytes, &off))
         return fail(NB_ERR_OOM, "engine: the request's footprint does not fit in the free arena");
     // ensure the group exists (D, counts) before building the problem
-    nb_status s = ensure_group(g, n, 0, 0);
+    NGroup &G = mixed ? g->mgroups[n] : g->groups[n];
+    nb_status s = ensure_group(g, G, n, 0, 0);
     if (s != NB_OK) { g->arena.release(off, bytes); return s; }
     char *base = g->arena.base + off;
     ProbDesc &P = g->h_desc[slot];
     memset(&P, 0, sizeof P);
     P.m = m;
+    P.prec = mixed ? NB_MIXED : NB_FP64;
     P.g = (float2 *)base;
-    P.r = (double *)(base + parts[0]);
-    P.p = (double *)(base + parts[0] + parts[1]);
-    P.w = (double *)(base + parts[0] + 2 * parts[1]);
-    P.x = (double *)(base + parts[0] + 3 * parts[1]);
-    P.partials = (double *)(base + parts[0] + 4 * parts[1]);
+    size_t at = parts[0];
+    if (mixed) {
+        P.f = (double *)(base + at); at += parts[1];
+        P.w = (double *)(base + at); at += parts[1];
+        P.x = (double *)(base + at); at += parts[1];
+        P.partials = (double *)(base + at); at += parts[2];
+        P.g32 = (float *)(base + at); at += parts[3];
+        P.r32 = (float *)(base + at); at += parts[4];
+        P.p32 = (float *)(base + at); at += parts[4];
+        P.w32 = (float *)(base + at); at += parts[4];
+        P.z32 = (float *)(base + at); at += parts[4];
+        P.inner_tol = inner_tol > 0.0 ? inner_tol : 1e-4;
+        P.max_outer = 50;
+    } else {
+        P.r = (double *)(base + at); at += parts[1];
+        P.p = (double *)(base + at); at += parts[1];
+        P.w = (double *)(base + at); at += parts[1];
+        P.x = (double *)(base + at); at += parts[1];
+        P.partials = (double *)(base + at); at += parts[2];
+    }
     P.te = te;
     shared_counts(m, P.cx, P.cy, P.cz);
     P.ntile_ax = (int)((m.E + te - 1) / te);
@@ -695,48 +1158,75 @@ nb_status engine_submit_internal(nb_engine *g, nb_box box, int n, double amp, co
     P.ntile_ds = total > 0 ? (int)((total + kDsTile - 1) / kDsTile) : 1;
     P.sc.tol = tol;
     P.sc.maxit = maxit;
-    P.sc.done = 1;   // not iterated until the start kernel has run
+    P.sc.done = 1;   // not iterated until set up
+    P.si.done = 1;
+    P.phase = kPhaseDone;
     cudaError_t e;
     if ((e = cudaMemcpyAsync(g->d_desc + slot, &P, sizeof(ProbDesc), cudaMemcpyHostToDevice, g->stream)) != cudaSuccess) {
         g->arena.release(off, bytes);
         return cuda_fail(e, "engine: descriptor upload");
     }
-    int *d_bad = (int *)(P.partials);   // scratch: the partials are rewritten by the start kernel
+    int *d_bad = (int *)(P.partials);   // scratch: the partials are rewritten before they are read
+    double *rhs = mixed ? P.f : P.r;
     NB_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), g->stream));
-    s = launch_box_geometry_pairs(m, amp, s3, g->groups[n].D, P.g, d_bad, g->stream);
+    s = launch_box_geometry_pairs(m, amp, s3, G.D, P.g, d_bad, g->stream);
     if (s == NB_OK && !f_unique &&
-        (e = cudaMemcpyAsync(P.r, f, sizeof(double) * m.npts, cudaMemcpyDeviceToDevice, g->stream)) != cudaSuccess)
+        (e = cudaMemcpyAsync(rhs, f, sizeof(double) * m.npts, cudaMemcpyDeviceToDevice, g->stream)) != cudaSuccess)
         s = cuda_fail(e, "engine: copy rhs");
     if (s == NB_OK && f_unique) {
-        eng_scatter_mask<<<grid_blocks(m.npts, 256, g->sms * 8), 256, 0, g->stream>>>(g->d_desc, slot, f);
+        eng_scatter_mask<<<grid_blocks(m.npts, 256, g->sms * 8), 256, 0, g->stream>>>(g->d_desc, slot, f, rhs);
         if ((e = cudaGetLastError()) != cudaSuccess) s = cuda_fail(e, "eng_scatter_mask");
+    }
+    if (s == NB_OK && mixed) {
+        const int64_t ng = (int64_t)6 * m.n * m.n * m.n * m.E;
+        eng_pairs_to_f32<<<grid_blocks(ng, 256, g->sms * 8), 256, 0, g->stream>>>(P.g, P.g32, ng);
+        if ((e = cudaGetLastError()) != cudaSuccess) s = cuda_fail(e, "eng_pairs_to_f32");
+        if (s == NB_OK && (e = cudaMemsetAsync(P.x, 0, sizeof(double) * m.npts, g->stream)) != cudaSuccess)
+            s = cuda_fail(e, "engine: clear x");
     }
     int bad = 0;
     if (s == NB_OK && (e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, g->stream)) != cudaSuccess)
         s = cuda_fail(e, "engine: geometry flag");
     if (s == NB_OK && (e = cudaStreamSynchronize(g->stream)) != cudaSuccess) s = cuda_fail(e, "engine: setup");
     if (s == NB_OK && bad) s = fail(NB_ERR_ARG, "engine: the perturbed map folds (|J| <= 0)");
-    if (s == NB_OK) s = dispatch_start(g, n, slot, P.ntile_ax);
+    if (s == NB_OK && !mixed) s = dispatch_start(g, n, slot, P.ntile_ax);
+    if (s == NB_OK && mixed) {
+        // the first outer pass (of the next step) forms r = f, <f,f>_c and
+        // starts the first inner solve
+        P.sc.done = maxit == 0 ? 1 : 0;
+        P.phase = maxit == 0 ? kPhaseDone : kPhaseOuter;
+        if ((e = cudaMemcpyAsync(g->d_desc + slot, &P, sizeof(ProbDesc), cudaMemcpyHostToDevice, g->stream)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(g->stream)) != cudaSuccess)
+            s = cuda_fail(e, "engine: descriptor upload");
+    }
     if (s != NB_OK) {
         g->arena.release(off, bytes);
         return s;
     }
     g->slots[slot].used = true;
     g->slots[slot].n = n;
+    g->slots[slot].prec = P.prec;
     g->slots[slot].off = off;
     g->slots[slot].bytes = bytes;
-    g->groups[n].slots.push_back(slot);
-    g->groups[n].dirty = true;
+    G.slots.push_back(slot);
+    G.dirty = true;
     *id = slot;
     return NB_OK;
 }
 
+// One engine step is a captured graph of `chunk` iterations: first the
+// outer pass of every n with mixed requests, then per iteration one CG
+// iteration per n of FP64 requests and one inner iteration per n of mixed
+// requests.
 nb_status engine_step_internal(nb_engine *g, int iters) {
     nb_status s = refresh_tiles(g);
     if (s != NB_OK) return s;
-    unsigned key = 0;
-    for (int n = 2; n <= kMaxN; n++)
-        if (!g->groups[n].slots.empty()) key |= 1u << n;
+    unsigned long long key = 0;
+    for (int n = 2; n <= kMaxN; n++) {
+        if (!g->groups[n].slots.empty()) key |= 1ull << n;
+        if (!g->mgroups[n].slots.empty()) key |= 1ull << (32 + n);
+    }
     if (!key || iters <= 0) return NB_OK;
     const int chunk = 8;
     if (!g->graph || g->graph_key != key || g->graph_chunk != chunk) {
@@ -746,9 +1236,13 @@ nb_status engine_step_internal(nb_engine *g, int iters) {
         }
         cudaGraph_t gr = nullptr;
         NB_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+        for (int n = 2; n <= kMaxN && s == NB_OK; n++)
+            if (key & (1ull << (32 + n))) s = dispatch_mixed(g, n, true);
         for (int k = 0; k < chunk && s == NB_OK; k++)
-            for (int n = 2; n <= kMaxN && s == NB_OK; n++)
-                if (key & (1u << n)) s = dispatch_iteration(g, n);
+            for (int n = 2; n <= kMaxN && s == NB_OK; n++) {
+                if (key & (1ull << n)) s = dispatch_iteration(g, n);
+                if (s == NB_OK && (key & (1ull << (32 + n)))) s = dispatch_mixed(g, n, false);
+            }
         cudaError_t e = cudaStreamEndCapture(g->stream, &gr);
         if (s != NB_OK) {
             if (gr) cudaGraphDestroy(gr);
@@ -778,9 +1272,11 @@ nb_status engine_retire_internal(nb_engine *g, int id, double *x) {
     // mark inactive on the device before the slot can be reused
     ProbDesc dead = P;
     dead.sc.done = 1;
+    dead.si.done = 1;
+    dead.phase = kPhaseDone;
     NB_CUDA(cudaMemcpyAsync(g->d_desc + id, &dead, sizeof(ProbDesc), cudaMemcpyHostToDevice, g->stream));
     NB_CUDA(cudaStreamSynchronize(g->stream));
-    NGroup &G = g->groups[S.n];
+    NGroup &G = S.prec == NB_MIXED ? g->mgroups[S.n] : g->groups[S.n];
     for (size_t k = 0; k < G.slots.size(); k++)
         if (G.slots[k] == id) { G.slots.erase(G.slots.begin() + k); break; }
     G.dirty = true;
@@ -836,8 +1332,8 @@ nb_status nb_engine_destroy(nb_engine *g) {
     if (!g) return NB_OK;
     if (g->stream) cudaStreamSynchronize(g->stream);
     if (g->graph) cudaGraphExecDestroy(g->graph);
-    for (int n = 0; n <= kMaxN; n++) {
-        NGroup &G = g->groups[n];
+    for (int gi = 0; gi < 2 * (kMaxN + 1); gi++) {
+        NGroup &G = gi <= kMaxN ? g->groups[gi] : g->mgroups[gi - kMaxN - 1];
         if (G.d_ax) cudaFree(G.d_ax);
         if (G.d_ds) cudaFree(G.d_ds);
         if (G.d_cnt) cudaFree(G.d_cnt);
@@ -849,11 +1345,12 @@ nb_status nb_engine_destroy(nb_engine *g) {
     return NB_OK;
 }
 
-nb_status nb_engine_footprint(nb_box mesh, int n, size_t *bytes) {
+nb_status nb_engine_footprint(nb_box mesh, int n, nb_precision prec, size_t *bytes) {
     if (!bytes) return fail(NB_ERR_ARG, "NULL argument");
     if (n < 2 || n > kMaxN || mesh.ex < 1 || mesh.ey < 1 || mesh.ez < 1) return fail(NB_ERR_ARG, "bad mesh");
-    size_t parts[3];
-    *bytes = desc_footprint(make_mesh(mesh, n), 4, parts);
+    if (prec != NB_FP64 && prec != NB_MIXED) return fail(NB_ERR_ARG, "unknown precision");
+    size_t parts[5];
+    *bytes = desc_footprint(make_mesh(mesh, n), (int)prec, parts);
     return NB_OK;
 }
 
@@ -863,11 +1360,12 @@ nb_status nb_engine_submit(nb_engine *g, const nb_request *req, const double *f_
         if (req->n < 2 || req->n > kMaxN || req->mesh.ex < 1 || req->mesh.ey < 1 || req->mesh.ez < 1)
             return fail(NB_ERR_ARG, "bad mesh");
         if (req->maxit < 0) return fail(NB_ERR_ARG, "maxit must be >= 0");
+        if (req->prec != NB_FP64 && req->prec != NB_MIXED) return fail(NB_ERR_ARG, "unknown precision");
         if (((uintptr_t)f_dev & 7u)) return fail(NB_ERR_ARG, "f must be 8-byte aligned");
         nb_status s = autotune(g, req->n);
         if (s != NB_OK) return s;
         return engine_submit_internal(g, req->mesh, req->n, req->amp, req->s, req->tol, req->maxit, f_dev,
-                                      g->groups[req->n].te, id_out);
+                                      g->groups[req->n].te, id_out, false, (int)req->prec, req->inner_tol);
     } catch (...) {
         return fail(NB_ERR_OOM, "engine: host allocation failed");
     }
@@ -879,11 +1377,12 @@ nb_status nb_engine_submit_unique(nb_engine *g, const nb_request *req, const dou
         if (req->n < 2 || req->n > kMaxN || req->mesh.ex < 1 || req->mesh.ey < 1 || req->mesh.ez < 1)
             return fail(NB_ERR_ARG, "bad mesh");
         if (req->maxit < 0) return fail(NB_ERR_ARG, "maxit must be >= 0");
+        if (req->prec != NB_FP64 && req->prec != NB_MIXED) return fail(NB_ERR_ARG, "unknown precision");
         if (((uintptr_t)fu_dev & 7u)) return fail(NB_ERR_ARG, "f must be 8-byte aligned");
         nb_status s = autotune(g, req->n);
         if (s != NB_OK) return s;
         return engine_submit_internal(g, req->mesh, req->n, req->amp, req->s, req->tol, req->maxit, fu_dev,
-                                      g->groups[req->n].te, id_out, true);
+                                      g->groups[req->n].te, id_out, true, (int)req->prec, req->inner_tol);
     } catch (...) {
         return fail(NB_ERR_OOM, "engine: host allocation failed");
     }
@@ -903,14 +1402,21 @@ nb_status nb_engine_poll(nb_engine *g, int id, int *done, int *iters, double *re
     const CgScalars &sc = g->h_desc[id].sc;
     if (done) *done = sc.done;
     if (iters) *iters = sc.it;
-    if (relres) *relres = sc.fnorm2 > 0.0 ? sqrt(sc.rho) / sqrt(sc.fnorm2) : 0.0;
+    if (relres) *relres = sc.fnorm2 > 0.0 ? sqrt(sc.rr) / sqrt(sc.fnorm2) : 0.0;
     if (status) {
         nb_status st = NB_OK;
         if (sc.status == (int)NB_ERR_BREAKDOWN) st = NB_ERR_BREAKDOWN;
-        else if (sc.done && sc.tol > 0.0 && sc.rho != 0.0 && !(sqrt(sc.rho) / sqrt(sc.fnorm2) <= sc.tol))
+        else if (sc.done && sc.tol > 0.0 && sc.rr != 0.0 && !(sqrt(sc.rr) / sqrt(sc.fnorm2) <= sc.tol))
             st = NB_ERR_NOT_CONVERGED;
         *status = (int)st;
     }
+    return NB_OK;
+}
+
+nb_status nb_engine_request_info(nb_engine *g, int id, int *prec, int *outer) {
+    if (!g || id < 0 || id >= kEngMaxSlots || !g->slots[id].used) return fail(NB_ERR_ARG, "unknown request id");
+    if (prec) *prec = g->h_desc[id].prec;
+    if (outer) *outer = g->h_desc[id].outer;
     return NB_OK;
 }
 

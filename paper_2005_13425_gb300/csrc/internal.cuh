@@ -106,7 +106,8 @@ struct nb_ctx {
     cudaGraphExec_t cg_graph32 = nullptr;
     int cg_graph32_chunk = 0;
     // mixed-precision parameters and statistics
-    double mixed_inner_tol = 1e-5;
+    bool f32_plain = false;             // FP32 ax_e without bulk staging (NEKGB_F32_STAGED=0)
+    double mixed_inner_tol = 1e-4;
     int mixed_max_outer = 50;
     int last_outer = 0;
     // timing

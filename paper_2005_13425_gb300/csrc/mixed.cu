@@ -8,7 +8,7 @@
 //
 //   x = x0
 //   loop: r = f - A x (FP64);  stop if sqrt(<r,r>_c/<f,f>_c) <= tol
-//         d = CG_fp32(A, r) to a relative inner residual (1e-5 by default)
+//         d = CG_fp32(A, r) to a relative inner residual (1e-4 by default)
 //         x += d (FP64)
 //
 // The inner CG is the fused three-kernel iteration of the FP64 solver on
@@ -225,7 +225,7 @@ nb_status cg_solve_mixed(nb_ctx *c, const double *f, double *x, double tol, int 
     nb_status s;
     if ((s = ensure_cg_workspace(c)) != NB_OK) return s;
     if (c->d_mask) return fail(NB_ERR_STATE, "the mixed-precision solve supports the box mask only");
-    const double inner_tol = c->mixed_inner_tol > 0.0 ? c->mixed_inner_tol : 1e-5;
+    const double inner_tol = c->mixed_inner_tol > 0.0 ? c->mixed_inner_tol : 1e-4;
     const int max_outer = c->mixed_max_outer > 0 ? c->mixed_max_outer : 50;
     const size_t bytes = sizeof(double) * c->m.npts;
     const int64_t np = c->m.npts;

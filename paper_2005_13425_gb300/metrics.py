@@ -9,13 +9,52 @@ words in and w out: 64 B per point in FP64, 32 B in FP32.
 """
 from __future__ import annotations
 
+import hashlib
 import json
 import os
+import re
 
 FALLBACK_HBM_GBS = 6800.0
 FALLBACK_BF16_TFLOPS = 1900.0
-# FP64 ALU ceiling: the recipe's nominal GB300 FP64 rate (TFLOP/s).
+# FP64 ALU ceiling: the nominal GB300 FP64 rate (TFLOP/s).
 NOMINAL_FP64_TFLOPS = 1.25
+# FP32-pipe ceiling of GB300: 152 SMs x 128 FP32 lanes x 2070 MHz maximum
+# SM clock, one FADD, FMUL or FFMA per lane per clock (10^12 instr/s).
+GB300_SMS = 152
+FP32_LANES_PER_SM = 128
+MAX_SM_MHZ = 2070.0
+FP32_PEAK_TOPS = GB300_SMS * FP32_LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
+
+# FP32-pipe instructions of the double-float building blocks (df.cuh):
+# TwoSum 6; first product (TwoProd + cross terms) 4; Dot2 step 12;
+# normalisation 3; pair addition 11.
+_TWO_SUM, _FIRST, _DOT2, _NORM, _ADD = 6, 4, 12, 3, 11
+
+
+def df_line_ops(n: int) -> int:
+    """FP32 instructions of one even-odd line product of n points: n/2 pair
+    sums and differences, then per output pair two Dot2 sums of n/2 terms
+    and two pair additions; odd n adds the middle term and middle output."""
+    h = n // 2
+    ops = 2 * h * _ADD
+    if n % 2 == 0:
+        ops += h * (2 * (_FIRST + _DOT2 * (h - 1)) + 2 * _ADD)
+    else:
+        ops += h * (2 * (_FIRST + _DOT2 * (h - 1)) + _DOT2 + 2 * _ADD)
+        ops += _FIRST + _DOT2 * h + _NORM
+    return ops
+
+
+def df_fp32_ops_per_point(n: int) -> float:
+    """FP32 instructions per point of the double-float ax_e (algorithmic:
+    the operation counts of the arithmetic as written, no overheads):
+    3 forward and 3 backward line products per point, the geometric
+    contraction (3 Dot2 sums of 3 terms, normalised), the sum of the three
+    partials (2 pair additions) and the 2 FP32 operations of the input
+    split."""
+    lines = 6 * df_line_ops(n) / n
+    contraction = 3 * (_FIRST + 2 * _DOT2 + _NORM)
+    return lines + contraction + 2 * _ADD + 2
 
 
 def cg_flops_per_point(n: int) -> int:
@@ -47,6 +86,12 @@ def ax_bytes_per_point(word: int = 8) -> int:
     return 8 * word
 
 
+def cg_head_bytes_per_point(word: int = 8) -> int:
+    """The fused CG head (x += alpha p, p = r + beta p, w = ax_e(p)): gxyz
+    (6 words), r, p and x read, p, x and w written: 12 words per point."""
+    return 12 * word
+
+
 def dssum_bytes_per_point(n: int, word: int = 8) -> float:
     """Read + write of the element-boundary fraction 1 - ((n-2)/n)^3."""
     frac = 1.0 - ((n - 2) / n) ** 3
@@ -62,3 +107,32 @@ def measured_peaks(root: str):
         return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
     except (OSError, KeyError, ValueError):
         return FALLBACK_HBM_GBS, FALLBACK_BF16_TFLOPS, "fallback"
+
+
+# Sources of the double-float CG head kernel; a recorded DRAM traffic figure
+# is valid only for the sources it was measured on.
+CG_HEAD_SOURCES = ("ax_df.cu", "ax_df_core.cuh", "df.cuh", "reduce.cuh")
+
+
+def source_digest(csrc_dir: str, names=CG_HEAD_SOURCES) -> str:
+    h = hashlib.sha256()
+    for nm in names:
+        with open(os.path.join(csrc_dir, nm), "rb") as fh:
+            h.update(nm.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(profile_path: str, digest: str):
+    """DRAM bytes per launch recorded in a profile summary (lines
+    'source_digest: <hex>' and 'traffic_bytes_per_launch: <int>'), or None
+    when the file is missing or was measured on other sources."""
+    try:
+        with open(profile_path) as fh:
+            text = fh.read()
+    except OSError:
+        return None
+    d = re.search(r"^source_digest:\s*([0-9a-f]+)\s*$", text, re.M)
+    t = re.search(r"^traffic_bytes_per_launch:\s*([0-9]+)\s*$", text, re.M)
+    if not d or not t or d.group(1) != digest:
+        return None
+    return int(t.group(1))

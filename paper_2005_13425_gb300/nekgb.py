@@ -49,7 +49,8 @@ class nb_info(ctypes.Structure):
 
 class nb_request(ctypes.Structure):
     _fields_ = [("mesh", nb_box), ("n", ctypes.c_int), ("amp", ctypes.c_double),
-                ("s", ctypes.c_double * 3), ("tol", ctypes.c_double), ("maxit", ctypes.c_int)]
+                ("s", ctypes.c_double * 3), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("prec", ctypes.c_int), ("inner_tol", ctypes.c_double)]
 
 
 _lib = None
@@ -86,11 +87,12 @@ _SIGS = {
     "nb_jacobi_diagonal": [_vp, _vp],
     "nb_engine_create": [ctypes.POINTER(_vp), ctypes.c_size_t, _vp],
     "nb_engine_destroy": [_vp],
-    "nb_engine_footprint": [nb_box, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
+    "nb_engine_footprint": [nb_box, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
     "nb_engine_submit": [_vp, ctypes.POINTER(nb_request), _vp, _ip],
     "nb_engine_submit_unique": [_vp, ctypes.POINTER(nb_request), _vp, _ip],
     "nb_engine_step": [_vp, ctypes.c_int],
     "nb_engine_poll": [_vp, ctypes.c_int, _ip, _ip, _dp, _ip],
+    "nb_engine_request_info": [_vp, ctypes.c_int, _ip, _ip],
     "nb_engine_retire": [_vp, ctypes.c_int, _vp],
     "nb_engine_stats": [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t), _ip],
     "nb_engine_tuning": [_vp, ctypes.c_int, _ip, _ip],
@@ -343,26 +345,29 @@ def nb_engine_destroy(eng):
     _check(load().nb_engine_destroy(eng), "nb_engine_destroy")
 
 
-def nb_engine_footprint(mesh, n) -> int:
+def nb_engine_footprint(mesh, n, prec=NB_FP64) -> int:
     b = ctypes.c_size_t(0)
-    _check(load().nb_engine_footprint(nb_box(*mesh), int(n), ctypes.byref(b)), "nb_engine_footprint")
+    _check(load().nb_engine_footprint(nb_box(*mesh), int(n), int(prec), ctypes.byref(b)), "nb_engine_footprint")
     return b.value
 
 
-def nb_engine_submit(eng, mesh, n, amp, s, tol, maxit, f, allow=(NB_OK,)):
+def _request(mesh, n, amp, s, tol, maxit, prec, inner_tol):
+    return nb_request(nb_box(*mesh), int(n), float(amp), (ctypes.c_double * 3)(*[float(v) for v in s]),
+                      float(tol), int(maxit), int(prec), float(inner_tol))
+
+
+def nb_engine_submit(eng, mesh, n, amp, s, tol, maxit, f, allow=(NB_OK,), prec=NB_FP64, inner_tol=0.0):
     """Returns (status, id); id is -1 when the request was not admitted."""
-    req = nb_request(nb_box(*mesh), int(n), float(amp), (ctypes.c_double * 3)(*[float(v) for v in s]),
-                     float(tol), int(maxit))
+    req = _request(mesh, n, amp, s, tol, maxit, prec, inner_tol)
     rid = ctypes.c_int(-1)
     st = load().nb_engine_submit(eng, ctypes.byref(req), _ptr(f, "torch.float64"), ctypes.byref(rid))
     _check(st, "nb_engine_submit", allow)
     return st, (rid.value if st == NB_OK else -1)
 
 
-def nb_engine_submit_unique(eng, mesh, n, amp, s, tol, maxit, fu, allow=(NB_OK,)):
+def nb_engine_submit_unique(eng, mesh, n, amp, s, tol, maxit, fu, allow=(NB_OK,), prec=NB_FP64, inner_tol=0.0):
     """nb_engine_submit with f given per unique node (device, NX*NY*NZ)."""
-    req = nb_request(nb_box(*mesh), int(n), float(amp), (ctypes.c_double * 3)(*[float(v) for v in s]),
-                     float(tol), int(maxit))
+    req = _request(mesh, n, amp, s, tol, maxit, prec, inner_tol)
     rid = ctypes.c_int(-1)
     st = load().nb_engine_submit_unique(eng, ctypes.byref(req), _ptr(fu, "torch.float64"), ctypes.byref(rid))
     _check(st, "nb_engine_submit_unique", allow)
@@ -380,6 +385,13 @@ def nb_engine_poll(eng, rid: int):
     _check(load().nb_engine_poll(eng, int(rid), ctypes.byref(d), ctypes.byref(it), ctypes.byref(rr),
                                  ctypes.byref(st)), "nb_engine_poll")
     return bool(d.value), it.value, rr.value, st.value
+
+
+def nb_engine_request_info(eng, rid: int):
+    """(precision, outer corrections so far)."""
+    p, o = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().nb_engine_request_info(eng, int(rid), ctypes.byref(p), ctypes.byref(o)), "nb_engine_request_info")
+    return p.value, o.value
 
 
 def nb_engine_retire(eng, rid: int, x=None):

@@ -26,15 +26,17 @@ def _rhs(torch, dims, n, seed):
     return torch.from_numpy(inputs.unique_field(*dims, n, seed=seed)).cuda()
 
 
-def footprint_total(nekgb, probs):
-    return sum(nekgb.nb_engine_footprint(p["dims"], p["n"]) for p in probs)
+def footprint_total(nekgb, probs, prec=0):
+    return sum(nekgb.nb_engine_footprint(p["dims"], p["n"], prec) for p in probs)
 
 
-def batched_run(nekgb, stream, probs, iters=100, sequential=True):
+def batched_run(nekgb, stream, probs, iters=100, sequential=True, prec=0):
     """Fixed-iteration batched solve of `probs` (dicts with dims, n,
-    mesh_seed, f_seed).  Returns throughput numbers."""
+    mesh_seed, f_seed).  Returns throughput numbers.  With prec = NB_MIXED
+    the iterations are inner (FP32) iterations of the defect correction, the
+    problems run with tol = 0, so they never stop early."""
     import torch
-    need = footprint_total(nekgb, probs)
+    need = footprint_total(nekgb, probs, prec)
     eng = nekgb.nb_engine_create(int(need * 1.1) + (64 << 20), stream)
     out = {"problems": len(probs), "iterations": iters}
     try:
@@ -44,7 +46,7 @@ def batched_run(nekgb, stream, probs, iters=100, sequential=True):
             q = next(p for p in probs if p["n"] == n)
             _, rid = nekgb.nb_engine_submit_unique(eng, q["dims"], n, inputs.PERTURB_AMP,
                                                    inputs.perturbation_coeffs(q["mesh_seed"]), 0.0, 8,
-                                                   rhs[probs.index(q)])
+                                                   rhs[probs.index(q)], prec=prec)
             nekgb.nb_engine_step(eng, 8)
             nekgb.nb_engine_retire(eng, rid)
         t0 = time.perf_counter()
@@ -52,7 +54,7 @@ def batched_run(nekgb, stream, probs, iters=100, sequential=True):
         for p, f in zip(probs, rhs):
             _, rid = nekgb.nb_engine_submit_unique(eng, p["dims"], p["n"], inputs.PERTURB_AMP,
                                                    inputs.perturbation_coeffs(p["mesh_seed"]), 0.0,
-                                                   iters, f)
+                                                   iters, f, prec=prec)
             ids.append(rid)
         out["setup_s"] = time.perf_counter() - t0
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -73,7 +75,7 @@ def batched_run(nekgb, stream, probs, iters=100, sequential=True):
             for p, f in zip(probs, rhs):
                 _, rid = nekgb.nb_engine_submit_unique(eng, p["dims"], p["n"], inputs.PERTURB_AMP,
                                                        inputs.perturbation_coeffs(p["mesh_seed"]),
-                                                       0.0, iters, f)
+                                                       0.0, iters, f, prec=prec)
                 stream.synchronize()
                 a.record(stream)
                 nekgb.nb_engine_step(eng, iters)
@@ -90,7 +92,7 @@ def batched_run(nekgb, stream, probs, iters=100, sequential=True):
     return out
 
 
-def measure_iterations(nekgb, stream, reqs, arena_bytes, step_iters=32):
+def measure_iterations(nekgb, stream, reqs, arena_bytes, step_iters=32, prec=0):
     """Iterations each request needs (solved together once, not timed)."""
     import torch
     eng = nekgb.nb_engine_create(arena_bytes, stream)
@@ -105,7 +107,7 @@ def measure_iterations(nekgb, stream, reqs, arena_bytes, step_iters=32):
                 st, rid = nekgb.nb_engine_submit_unique(
                     eng, r["dims"], r["n"], inputs.PERTURB_AMP, inputs.perturbation_coeffs(r["mesh_seed"]),
                     r["tol"], r["maxit"], _rhs(torch, r["dims"], r["n"], r["f_seed"]),
-                    allow=(nekgb.NB_OK, nekgb.NB_ERR_OOM))
+                    allow=(nekgb.NB_OK, nekgb.NB_ERR_OOM), prec=prec)
                 if st != nekgb.NB_OK:
                     break
                 active[rid] = k
@@ -122,9 +124,11 @@ def measure_iterations(nekgb, stream, reqs, arena_bytes, step_iters=32):
 
 
 def serving_run(nekgb, stream, reqs, utilisation, capacity_dof_its, iterations, arena_bytes,
-                step_iters=16, seed=11):
+                step_iters=16, seed=11, prec=0):
     """Poisson arrivals at a rate that offers `utilisation` x the measured
-    capacity (DOF-iterations per second).  Returns latency statistics."""
+    capacity (DOF-iterations per second).  The arrival times depend only on
+    the requests, the utilisation and the seed, so FP64 and mixed runs see
+    the same arrivals.  Returns latency statistics."""
     import torch
     work = np.array([r["E"] * r["n"] ** 3 * it for r, it in zip(reqs, iterations)], dtype=float)
     rate = utilisation * capacity_dof_its / work.mean()          # requests per second
@@ -140,7 +144,7 @@ def serving_run(nekgb, stream, reqs, utilisation, capacity_dof_its, iterations, 
             r = next(q for q in reqs if q["n"] == n)
             _, rid = nekgb.nb_engine_submit_unique(eng, r["dims"], n, inputs.PERTURB_AMP,
                                                    inputs.perturbation_coeffs(r["mesh_seed"]), 0.0, 1,
-                                                   rhs[reqs.index(r)])
+                                                   rhs[reqs.index(r)], prec=prec)
             nekgb.nb_engine_step(eng, 8)
             nekgb.nb_engine_retire(eng, rid)
         t0 = time.perf_counter()
@@ -156,7 +160,7 @@ def serving_run(nekgb, stream, reqs, utilisation, capacity_dof_its, iterations, 
                 r = reqs[k]
                 st, rid = nekgb.nb_engine_submit_unique(
                     eng, r["dims"], r["n"], inputs.PERTURB_AMP, inputs.perturbation_coeffs(r["mesh_seed"]),
-                    r["tol"], r["maxit"], rhs[k], allow=(nekgb.NB_OK, nekgb.NB_ERR_OOM))
+                    r["tol"], r["maxit"], rhs[k], allow=(nekgb.NB_OK, nekgb.NB_ERR_OOM), prec=prec)
                 if st != nekgb.NB_OK:
                     break
                 active[rid] = k
@@ -177,7 +181,8 @@ def serving_run(nekgb, stream, reqs, utilisation, capacity_dof_its, iterations, 
     finally:
         nekgb.nb_engine_destroy(eng)
     lat_ms = np.array(lat) * 1e3
-    return {"requests": len(reqs), "utilisation_target": utilisation, "rate_per_s": rate,
+    return {"precision": "mixed" if prec else "fp64",
+            "requests": len(reqs), "utilisation_target": utilisation, "rate_per_s": rate,
             "solves_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat_ms, 50)),
             "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean()),
             "max_relres_over_tol": float(max(rr / r["tol"] for rr, r in zip(relres, reqs)))}

@@ -6,6 +6,9 @@
   mix of other problems (per-problem tiles and fixed-order reductions).
 * Admission is by arena footprint: too-large requests are refused with
   NB_ERR_OOM until retired requests free space.
+* Mixed-precision requests (FP32 inner CG, FP64 defect correction) reach
+  the FP64 tolerance in the oracle's operator, alone or next to FP64
+  requests, with bit-identical results in any mix.
 """
 import numpy as np
 import pytest
@@ -40,14 +43,15 @@ def problem(oracle, dims, n, pid):
 
 
 def run_engine(nek, items, arena=4 * GIB, iters_per_step=64, max_steps=400):
-    """items: list of (dims, n, s, f, tol, maxit).  Returns per-item (x, iters, relres, status)."""
+    """items: list of (dims, n, s, f, tol, maxit[, prec]).  Returns per-item
+    (x, iters, relres, status, outer corrections)."""
     stream = torch.cuda.current_stream()
     eng = nek.nb_engine_create(arena, stream)
     try:
         ids = []
-        for dims, n, s, f, tol, maxit in items:
+        for dims, n, s, f, tol, maxit, *prec in items:
             st, rid = nek.nb_engine_submit(eng, dims, n, inputs.PERTURB_AMP, s, tol, maxit,
-                                           torch.from_numpy(f).cuda())
+                                           torch.from_numpy(f).cuda(), prec=prec[0] if prec else nek.NB_FP64)
             ids.append(rid)
         out = [None] * len(items)
         for _ in range(max_steps):
@@ -56,10 +60,11 @@ def run_engine(nek, items, arena=4 * GIB, iters_per_step=64, max_steps=400):
                 if out[k] is None:
                     done, it, rr, st = nek.nb_engine_poll(eng, rid)
                     if done:
+                        _, outer = nek.nb_engine_request_info(eng, rid)
                         x = torch.empty(items[k][3].shape, dtype=torch.float64, device="cuda")
                         nek.nb_engine_retire(eng, rid, x)
                         stream.synchronize()
-                        out[k] = (x.cpu().numpy(), it, rr, st)
+                        out[k] = (x.cpu().numpy(), it, rr, st, outer)
             if all(o is not None for o in out):
                 break
         return out
@@ -80,7 +85,7 @@ def test_engine_batch_converges_against_oracle(nek, oracle):
         probs.append((dims, n, P, f))
         items.append((dims, n, s, f, 1e-10, 5000))
     out = run_engine(nek, items)
-    for (dims, n, P, f), (x, it, rr, st) in zip(probs, out):
+    for (dims, n, P, f), (x, it, rr, st, _) in zip(probs, out):
         assert st == nek.NB_OK and rr <= 1e-10 and it > 0
         assert true_relres(oracle, dims, n, P, f, x) <= 2e-10
 
@@ -102,7 +107,7 @@ def test_engine_alone_equals_mix(nek, oracle):
 def test_engine_fixed_iterations_match_single_solver(nek, oracle):
     dims, n = (3, 3, 2), 6
     P, s, f = problem(oracle, dims, n, 3)
-    x_eng, it, rr, st = run_engine(nek, [(dims, n, s, f, 0.0, 24)], iters_per_step=8)[0]
+    x_eng, it, rr, st, _ = run_engine(nek, [(dims, n, s, f, 0.0, 24)], iters_per_step=8)[0]
     assert it == 24
     x_ref, it_ref, rr_ref, _, _ = oracle.cg(*dims, n, P["D"], P["gxyz"], P["mask"], f, tol=0.0, maxit=24)
     assert np.abs(x_eng - x_ref).max() <= 1e-8 * np.abs(x_ref).max()
@@ -129,3 +134,51 @@ def test_engine_admission_by_footprint(nek, oracle):
         nek.nb_engine_retire(eng, c)
     finally:
         nek.nb_engine_destroy(eng)
+
+
+def test_engine_mixed_converges_against_oracle(nek, oracle):
+    specs = [((2, 2, 2), 6), ((4, 2, 2), 8), ((2, 2, 1), 10), ((3, 3, 2), 12)]
+    items, probs = [], []
+    for pid, (dims, n) in enumerate(specs):
+        P, s, f = problem(oracle, dims, n, 40 + pid)
+        probs.append((dims, n, P, f))
+        items.append((dims, n, s, f, 1e-10, 20000, nek.NB_MIXED))
+    # one FP64 request in the same engine
+    P, s, f = problem(oracle, (3, 2, 2), 8, 49)
+    probs.append(((3, 2, 2), 8, P, f))
+    items.append(((3, 2, 2), 8, s, f, 1e-10, 5000, nek.NB_FP64))
+    out = run_engine(nek, items, iters_per_step=32)
+    for k, ((dims, n, P, f), (x, it, rr, st, outer)) in enumerate(zip(probs, out)):
+        assert st == nek.NB_OK and rr <= 1e-10 and it > 0
+        assert true_relres(oracle, dims, n, P, f, x) <= 2e-10
+        if k < len(specs):
+            assert outer >= 2          # at least one correction after the first inner solve
+        else:
+            assert outer == 0
+
+
+def test_engine_mixed_alone_equals_mix(nek, oracle):
+    target = ((3, 2, 2), 10)
+    P, s, f = problem(oracle, *target, 57)
+    item = (target[0], target[1], s, f, 1e-10, 20000, nek.NB_MIXED)
+    alone = run_engine(nek, [item], iters_per_step=16)[0]
+    others = []
+    for pid, (dims, n, prec) in enumerate([((2, 2, 2), 6, nek.NB_MIXED), ((4, 4, 2), 8, nek.NB_FP64),
+                                           ((2, 1, 1), 10, nek.NB_MIXED)]):
+        _, s2, f2 = problem(oracle, dims, n, 60 + pid)
+        others.append((dims, n, s2, f2, 1e-9, 3000, prec))
+    mixed = run_engine(nek, others[:2] + [item] + others[2:], iters_per_step=16)[2]
+    assert alone[1] == mixed[1] and alone[2] == mixed[2] and alone[4] == mixed[4]
+    assert np.array_equal(alone[0], mixed[0])          # bit-identical
+
+
+def test_engine_mixed_footprint_and_budget(nek, oracle):
+    dims, n = (3, 2, 2), 8
+    f64 = nek.nb_engine_footprint(dims, n, nek.NB_FP64)
+    fmx = nek.nb_engine_footprint(dims, n, nek.NB_MIXED)
+    pts = 12 * n ** 3
+    assert fmx > f64 and fmx - f64 >= (72 + 40 - 48 - 32) * pts
+    # a budget too small to converge ends the request with NB_ERR_NOT_CONVERGED
+    P, s, f = problem(oracle, dims, n, 70)
+    x, it, rr, st, outer = run_engine(nek, [(dims, n, s, f, 1e-12, 10, nek.NB_MIXED)], iters_per_step=8)[0]
+    assert st == nek.NB_ERR_NOT_CONVERGED and 0 < it <= 10 and rr > 1e-12

@@ -23,3 +23,38 @@ def test_paper_printed_rooflines():
         got = metrics.roofline_gflops(float(bw), int(n))
         # the paper prints whole GFlop/s, truncated (900 x 154/240 = 577.5 -> 577)
         assert int(got) == int(printed), (got, printed)
+
+
+def _count_line_eo(n):
+    """Count the FP32 instructions of an even-odd line product by walking
+    its steps (pair sums/differences, Dot2 chains, output pair additions)."""
+    first, dot2, norm, add = 4, 12, 3, 11
+    h = n // 2
+    ops = 0
+    for _ in range(h):
+        ops += 2 * add                       # x_l + x_{n-1-l}, x_l - x_{n-1-l}
+    for _ in range(h):
+        for chain_len in (h, h + (n % 2)):   # P over differences, Q over sums (+ middle)
+            ops += first + dot2 * (chain_len - 1)
+        ops += 2 * add                       # y_m = P + Q, y_{n-1-m} = P - Q
+    if n % 2:
+        ops += first + dot2 * h + norm       # middle output
+    return ops
+
+
+def test_double_float_op_counts():
+    for n in range(2, 17):
+        assert metrics.df_line_ops(n) == _count_line_eo(n)
+    # n = 10: 74 per point per line product, 6 line products, 93 for the
+    # contraction, 22 for the partial sums, 2 for the split
+    assert metrics.df_fp32_ops_per_point(10) == 6 * 74 + 93 + 22 + 2
+    assert abs(metrics.FP32_PEAK_TOPS - 152 * 128 * 2.07e9 / 1e12) < 1e-9
+    assert metrics.cg_head_bytes_per_point() == 96
+
+
+def test_recorded_traffic_needs_matching_digest(tmp_path):
+    p = tmp_path / "prof.md"
+    p.write_text("# summary\nsource_digest: abcdef0123456789\ntraffic_bytes_per_launch: 393216000\n")
+    assert metrics.recorded_traffic(str(p), "abcdef0123456789") == 393216000
+    assert metrics.recorded_traffic(str(p), "0000000000000000") is None
+    assert metrics.recorded_traffic(str(tmp_path / "missing.md"), "abcdef0123456789") is None

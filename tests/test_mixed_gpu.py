@@ -141,3 +141,47 @@ def test_mixed_params_and_errors(nek, oracle):
         assert ei.value.status == nek.NB_ERR_STATE
     finally:
         nek.nb_destroy(h)
+
+
+def _ctx_with_staging(nek, P, dims, n, staged):
+    import os
+    old = os.environ.get("NEKGB_F32_STAGED")
+    os.environ["NEKGB_F32_STAGED"] = "1" if staged else "0"
+    try:
+        return mixed_ctx(nek, P, dims, n)
+    finally:
+        if old is None:
+            del os.environ["NEKGB_F32_STAGED"]
+        else:
+            os.environ["NEKGB_F32_STAGED"] = old
+
+
+@pytest.mark.parametrize("dims,n", [((9, 8, 6), 6), ((7, 7, 7), 10), ((3, 2, 1), 8)])
+def test_f32_staged_operator_and_solve_match_plain(nek, oracle, dims, n):
+    """The bulk-copy staged FP32 kernel (two elements in flight per CTA; the
+    meshes have more elements than resident CTAs, so the stage ring turns
+    over) computes the same arithmetic as the plain kernel: bit-identical
+    operator output and inner CG, and the oracle's operator to FP32
+    tolerance."""
+    P = oracle.box_problem(*dims, n, 0.05, inputs.perturbation_coeffs(3))
+    u = inputs.local_field(P["E"], n, seed=n + 1)
+    want = oracle.ax_e(P["D"], P["gxyz"], u)
+    fu = inputs.unique_field(*dims, n, seed=4)
+    f = oracle.apply_mask(P["mask"], oracle.scatter_unique(*dims, n, fu))
+    outs = []
+    for staged in (True, False):
+        h = _ctx_with_staging(nek, P, dims, n, staged)
+        try:
+            w = torch.empty(P["E"], n ** 3, dtype=torch.float32, device="cuda")
+            nek.nb_ax_f32(h, dev(u.astype(np.float32)), w)
+            x = torch.zeros_like(dev(f))
+            st, it, rr = nek.nb_cg_solve(h, dev(f), x, tol=1e-10, maxit=20000)
+            outs.append((host(w), host(x), it, rr))
+        finally:
+            nek.nb_destroy(h)
+    (w1, x1, it1, rr1), (w0, x0, it0, rr0) = outs
+    assert np.array_equal(w1, w0)
+    assert it1 == it0 and rr1 == rr0 and np.array_equal(x1, x0)
+    err = np.abs(w1.astype(np.float64) - want).max() / np.abs(want).max()
+    assert err <= 2e-5, err
+    assert rr1 <= 1e-10
