@@ -156,17 +156,44 @@ struct DfElemIO {
     const float2 *g;    // gxyz pairs [6][n^3] of the element, scaled by 2^-(gexp-1023)
 };
 
+// Points of an element per thread of a T-thread CTA in the pointwise phases.
+template <int N, int T>
+__host__ __device__ constexpr int df_points_per_thread() {
+    return (N * N * N + T - 1) / T;
+}
+
+// This thread's point-face masks (point_faces of q = threadIdx.x + k T),
+// computed once per kernel for df_element's fused CG head.
+template <int N, int T>
+__device__ __forceinline__ void df_point_masks(unsigned *pf) {
+#pragma unroll
+    for (int k = 0; k < df_points_per_thread<N, T>(); k++) {
+        const int q = threadIdx.x + k * T;
+        pf[k] = q < N * N * N ? point_faces<N>(q) : 0u;
+    }
+}
+
+// Faces of element (ex,ey,ez) on the box boundary, in point_faces' bit order.
+__device__ __forceinline__ unsigned box_faces(int ex, int ey, int ez, const Mesh &m) {
+    return (unsigned)(ex == 0) | ((unsigned)(ex == m.ex - 1) << 1) | ((unsigned)(ey == 0) << 2) |
+           ((unsigned)(ey == m.ey - 1) << 3) | ((unsigned)(ez == 0) << 4) | ((unsigned)(ez == m.ez - 1) << 5);
+}
+
 // One element of ax_e in double-float arithmetic, executed by the whole CTA
 // (every thread must call it; it contains barriers).  sm holds 6 n^3 pairs,
 // s_emax is a shared int that must be 0 on entry (left 0 on exit).
 // MODE 1 is the CG head: x += xa p, p = r + beta p, w = ax_e(p); with fuse,
 // box-face points of w are zeroed and the element-interior <w,p> is added
-// to dot.  (ex, ey, ez) is the element's position in the box m.
+// to dot; pf holds the thread's point-face masks (df_point_masks; null:
+// computed per point) and (ex, ey, ez) is the element's position in the box m.  The geometric
+// factors and x are loaded with the streaming (evict-first) cache policy:
+// they are not read again in the iteration, which keeps w and p in L2 for
+// the dssum and update kernels that follow.
 template <int N, int MODE, bool EO, int T = ax_df_threads(N)>
 __device__ __forceinline__ void df_element(const DfElemIO &io, double beta, double xa, bool fuse,
                                            int gexp, const Mesh &m, int ex, int ey, int ez,
                                            const typename DfConsts<N, EO>::type &D, float2 *sm,
-                                           int *s_emax, double &dot) {
+                                           int *s_emax, double &dot, const unsigned *pf = nullptr) {
     constexpr int N2 = N * N, N3 = N * N * N;
     float2 *U = sm;            // input pairs; later the r-partial of w
     float2 *W0 = sm + N3;      // wr -> ur
@@ -191,7 +218,7 @@ __device__ __forceinline__ void df_element(const DfElemIO &io, double beta, doub
     } else if (io.minv) {
         for (int q = t; q < N3; q += T) {
             const double pold = io.p[q];
-            if (xa != 0.0) io.x[q] = fma(xa, pold, io.x[q]);
+            if (xa != 0.0) __stcs(io.x + q, fma(xa, pold, __ldcs(io.x + q)));
             const double v = fma(beta, pold, io.r[q] * io.minv[q]);
             io.p[q] = v;
             stage(v, q);
@@ -199,7 +226,7 @@ __device__ __forceinline__ void df_element(const DfElemIO &io, double beta, doub
     } else if (xa != 0.0) {
         for (int q = t; q < N3; q += T) {
             const double pold = io.p[q];
-            io.x[q] = fma(xa, pold, io.x[q]);
+            __stcs(io.x + q, fma(xa, pold, __ldcs(io.x + q)));
             const double v = fma(beta, pold, io.r[q]);
             io.p[q] = v;
             stage(v, q);
@@ -239,8 +266,8 @@ __device__ __forceinline__ void df_element(const DfElemIO &io, double beta, doub
     const float2 *g = io.g;
     for (int q = t; q < N3; q += T) {
         const float2 wr = W0[q], ws = W1[q], wt = W2[q];
-        const float2 g0 = g[q], g1 = g[N3 + q], g2 = g[2 * N3 + q];
-        const float2 g3 = g[3 * N3 + q], g4 = g[4 * N3 + q], g5 = g[5 * N3 + q];
+        const float2 g0 = __ldcs(g + q), g1 = __ldcs(g + N3 + q), g2 = __ldcs(g + 2 * N3 + q);
+        const float2 g3 = __ldcs(g + 3 * N3 + q), g4 = __ldcs(g + 4 * N3 + q), g5 = __ldcs(g + 5 * N3 + q);
         dfa::Acc r = dfa::first(g0.x, g0.y, wr.x, wr.y);
         dfa::fma(r, g1.x, g1.y, ws.x, ws.y);
         dfa::fma(r, g2.x, g2.y, wt.x, wt.y);
@@ -270,20 +297,29 @@ __device__ __forceinline__ void df_element(const DfElemIO &io, double beta, doub
     __syncthreads();
 
     // ---- w = r-partial + s-partial + t-partial, scaled back, FP64 out
-    for (int q = t; q < N3; q += T) {
-        const float2 s = dfa::add(dfa::add(U[q], P1[q]), P2[q]);
-        double wv = dfa::join_scaled(s, sh_out);
-        if (MODE == 1 && fuse) {
-            // Dirichlet points are zeroed before dssum (their sum is then
-            // +0, as mask-after-dssum gives); element-interior points have
-            // multiplicity 1 and are final: <w,p> here.
-            const int i = q % N, j = (q / N) % N, k = q / N2;
-            if (on_box_face(i, j, k, ex, ey, ez, m))
+    if (MODE == 1 && fuse) {
+        // Dirichlet points are zeroed before dssum (their sum is then +0, as
+        // mask-after-dssum gives); element-interior points (no face bit)
+        // have multiplicity 1 and are final: <w,p> here.
+        const unsigned bf = box_faces(ex, ey, ez, m);
+#pragma unroll
+        for (int k = 0; k < df_points_per_thread<N, T>(); k++) {
+            const int q = t + k * T;
+            if (df_points_per_thread<N, T>() * T != N3 && q >= N3) break;
+            const float2 s = dfa::add(dfa::add(U[q], P1[q]), P2[q]);
+            double wv = dfa::join_scaled(s, sh_out);
+            const unsigned f = pf ? pf[k] : point_faces<N>(q);
+            if (f & bf)
                 wv = 0.0;
-            else if (i > 0 && i < N - 1 && j > 0 && j < N - 1 && k > 0 && k < N - 1)
+            else if (f == 0u)
                 dot = fma(wv, io.p[q], dot);
+            io.w[q] = wv;
         }
-        io.w[q] = wv;
+    } else {
+        for (int q = t; q < N3; q += T) {
+            const float2 s = dfa::add(dfa::add(U[q], P1[q]), P2[q]);
+            io.w[q] = dfa::join_scaled(s, sh_out);
+        }
     }
     if (t == 0) *s_emax = 0;
     __syncthreads();

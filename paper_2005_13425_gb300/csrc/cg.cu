@@ -136,16 +136,25 @@ __device__ __forceinline__ void update_body(double *__restrict__ r, const double
                                             double alpha, const double *__restrict__ minv, double &acc,
                                             double &accz) {
     constexpr int N3 = N * N * N;
+    constexpr int K = (N3 + kRedThreads - 1) / kRedThreads;   // points per thread per element
+    unsigned pf[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const int q = threadIdx.x + k * kRedThreads;
+        pf[k] = q < N3 ? point_faces<N>(q) : 0u;
+    }
     for (int64_t e = blockIdx.x; e < m.E; e += gridDim.x) {
         int ex, ey, ez;
         element_coords(e, m, ex, ey, ez);
+        const unsigned sf = shared_faces(ex, ey, ez, m);
         const int64_t base = e * N3;
-#pragma unroll 4
-        for (int q = threadIdx.x; q < N3; q += kRedThreads) {
-            const int i = q % N, j = (q / N) % N, k = q / (N * N);
-            const double rn = fma(-alpha, w[base + q], r[base + q]);
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const int q = threadIdx.x + k * kRedThreads;
+            if (K * kRedThreads != N3 && q >= N3) break;
+            const double rn = fma(-alpha, __ldcs(w + base + q), r[base + q]);
             r[base + q] = rn;
-            const int lg = log2_mult(i, j, k, ex, ey, ez, m);
+            const int lg = __popc(pf[k] & sf);
             acc = fma(scale_down_pow2(rn, lg), rn, acc);
             if (PRE) accz = fma(scale_down_pow2(rn * minv[base + q], lg), rn, accz);
         }

@@ -30,6 +30,7 @@
 
 #include "ax_df_core.cuh"
 #include "ax_f32_core.cuh"
+#include "gs_fast.cuh"
 #include "gs_nodes.cuh"
 #include "internal.cuh"
 #include "reduce.cuh"
@@ -61,6 +62,7 @@ struct ProbDesc {
     CgScalars si;
     int phase, outer, max_outer, pad;
     double inner_tol;
+    DsCat dd;                   // shared-node decode of the mesh (by category)
     double *f;                  // mixed: right-hand side (FP64, masked)
     float *g32;                 // mixed: gxyz FP32 [E][6][n^3]
     float *r32, *p32, *w32, *z32;
@@ -110,6 +112,7 @@ eng_ax_head(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const i
 
 // dssum of w over (slot, node tile) work units, shared-node <w,p>_c, and in
 // the problem's last tile: alpha = rho/<w,p>_c.
+template <int N>
 __global__ void __launch_bounds__(kEngThreads)
 eng_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles) {
     __shared__ double red[32];
@@ -119,7 +122,6 @@ eng_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int
         const int2 tile = tiles[ti];
         ProbDesc &P = desc[tile.x];
         if (P.sc.done) continue;
-        const Mesh m = P.m;
         const int total = P.cx + P.cy + P.cz;
         double *w = P.w;
         const double *p = P.p;
@@ -127,10 +129,8 @@ eng_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int
         const int q0 = tile.y * kDsTile;
         const int q1 = q0 + kDsTile < total ? q0 + kDsTile : total;
         for (int q = q0 + threadIdx.x; q < q1; q += kEngThreads) {
-            int gx, gy, gz;
-            shared_node(q, m, P.cx, P.cy, gx, gy, gz);
             int64_t idx[8];
-            const int c = node_copies(gx, gy, gz, m, idx);
+            const int c = cat_copies<N>(q, P.dd, idx);
             double s;
             double ps;
             int lg;
@@ -201,8 +201,15 @@ template <int N>
 __global__ void __launch_bounds__(kEngThreads)
 eng_update(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles) {
     constexpr int N3 = N * N * N;
+    constexpr int K = (N3 + kEngThreads - 1) / kEngThreads;   // points per thread per element
     __shared__ double red[32];
     __shared__ int s_last;
+    unsigned pf[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const int q = threadIdx.x + k * kEngThreads;
+        pf[k] = q < N3 ? point_faces<N>(q) : 0u;
+    }
     const int nt = *ntiles;
     for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
         const int2 tile = tiles[ti];
@@ -216,14 +223,16 @@ eng_update(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const in
         for (int64_t e = e0; e < e1; e++) {
             int ex, ey, ez;
             element_coords(e, m, ex, ey, ez);
+            const unsigned sf = shared_faces(ex, ey, ez, m);
             double *r = P.r + e * N3;
             const double *w = P.w + e * N3;
-#pragma unroll 4
-            for (int q = threadIdx.x; q < N3; q += kEngThreads) {
-                const int i = q % N, j = (q / N) % N, k = q / (N * N);
-                const double rn = fma(-alpha, w[q], r[q]);
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const int q = threadIdx.x + k * kEngThreads;
+                if (K * kEngThreads != N3 && q >= N3) break;
+                const double rn = fma(-alpha, __ldcs(w + q), r[q]);
                 r[q] = rn;
-                acc = fma(scale_down_pow2(rn, log2_mult(i, j, k, ex, ey, ez, m)), rn, acc);
+                acc = fma(scale_down_pow2(rn, __popc(pf[k] & sf)), rn, acc);
             }
         }
         const double b = block_sum(acc, red);
@@ -388,7 +397,7 @@ eng_m_head(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const in
 // Shared-node sums of the FP32 w (and of the FP64 w in the outer pass, DOT
 // = false) over (slot, node tile) work units.  With DOT, the shared-node
 // <w,p>_c is accumulated and the problem's last tile forms alpha.
-template <typename T, bool DOT>
+template <typename T, bool DOT, int N>
 __global__ void __launch_bounds__(kEngThreads)
 eng_m_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles) {
     __shared__ double red[32];
@@ -402,7 +411,6 @@ eng_m_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const i
         } else {
             if (P.phase != kPhaseOuter || P.outer == 0) continue;   // x = 0 on the first pass: A x = 0
         }
-        const Mesh m = P.m;
         const int total = P.cx + P.cy + P.cz;
         T *w;
         const float *p = P.p32;
@@ -412,10 +420,8 @@ eng_m_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const i
         const int q0 = tile.y * kDsTile;
         const int q1 = q0 + kDsTile < total ? q0 + kDsTile : total;
         for (int q = q0 + threadIdx.x; q < q1; q += kEngThreads) {
-            int gx, gy, gz;
-            shared_node(q, m, P.cx, P.cy, gx, gy, gz);
             int64_t idx[8];
-            const int c = node_copies(gx, gy, gz, m, idx);
+            const int c = cat_copies<N>(q, P.dd, idx);
             T s;
             if (c == 2) {
                 s = plus_zero(w[idx[0]]) + w[idx[1]];
@@ -481,8 +487,15 @@ template <int N>
 __global__ void __launch_bounds__(kEngThreads)
 eng_m_update(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles) {
     constexpr int N3 = N * N * N;
+    constexpr int K = (N3 + kEngThreads - 1) / kEngThreads;   // points per thread per element
     __shared__ double red[32];
     __shared__ int s_last;
+    unsigned pf[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const int q = threadIdx.x + k * kEngThreads;
+        pf[k] = q < N3 ? point_faces<N>(q) : 0u;
+    }
     const int nt = *ntiles;
     for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
         const int2 tile = tiles[ti];
@@ -496,14 +509,16 @@ eng_m_update(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const 
         for (int64_t e = e0; e < e1; e++) {
             int ex, ey, ez;
             element_coords(e, m, ex, ey, ez);
+            const unsigned sf = shared_faces(ex, ey, ez, m);
             float *r = P.r32 + e * N3;
             const float *w = P.w32 + e * N3;
-#pragma unroll 4
-            for (int q = threadIdx.x; q < N3; q += kEngThreads) {
-                const int i = q % N, j = (q / N) % N, k = q / (N * N);
-                const float rn = fmaf(-alpha, w[q], r[q]);
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const int q = threadIdx.x + k * kEngThreads;
+                if (K * kEngThreads != N3 && q >= N3) break;
+                const float rn = fmaf(-alpha, __ldcs(w + q), r[q]);
                 r[q] = rn;
-                const float cw = __uint_as_float((unsigned)(127 - log2_mult(i, j, k, ex, ey, ez, m)) << 23);
+                const float cw = __uint_as_float((127u - __popc(pf[k] & sf)) << 23);   // 2^-lg
                 acc.add_prod(rn * cw, rn);
             }
         }
@@ -830,7 +845,7 @@ static nb_status group_iteration(nb_engine *g, const NGroup &G) {
     if constexpr (N >= 13) s = head_launch<N, 2>(g, G);
     else s = G.lpt == 2 ? head_launch<N, 2>(g, G) : head_launch<N, 1>(g, G);
     if (s != NB_OK) return s;
-    eng_dssum<<<g->sms * 8, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ds, G.d_cnt + 1);
+    eng_dssum<N><<<g->sms * 8, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ds, G.d_cnt + 1);
     NB_LAUNCH_CHECK("eng_dssum");
     eng_update<N><<<g->sms * 4, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ax, G.d_cnt);
     NB_LAUNCH_CHECK("eng_update");
@@ -879,7 +894,7 @@ static nb_status mixed_inner_iteration(nb_engine *g, const NGroup &G) {
     for (int q = 0; q < N * N; q++) D.d[q] = (float)G.D[q];
     eng_m_head<N, T><<<g->sms * occ, T, smem, g->stream>>>(g->d_desc, G.d_ax, G.d_cnt, D);
     NB_LAUNCH_CHECK("eng_m_head");
-    eng_m_dssum<float, true><<<g->sms * 8, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ds, G.d_cnt + 1);
+    eng_m_dssum<float, true, N><<<g->sms * 8, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ds, G.d_cnt + 1);
     NB_LAUNCH_CHECK("eng_m_dssum");
     eng_m_update<N><<<g->sms * 4, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ax, G.d_cnt);
     NB_LAUNCH_CHECK("eng_m_update");
@@ -905,7 +920,7 @@ static nb_status mixed_outer_pass(nb_engine *g, const NGroup &G) {
     NB_LAUNCH_CHECK("eng_m_outer_x");
     eng_m_outer_ax<N, T><<<g->sms * occ, T, smem, g->stream>>>(g->d_desc, G.d_ax, G.d_cnt, D);
     NB_LAUNCH_CHECK("eng_m_outer_ax");
-    eng_m_dssum<double, false><<<g->sms * 8, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ds, G.d_cnt + 1);
+    eng_m_dssum<double, false, N><<<g->sms * 8, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ds, G.d_cnt + 1);
     NB_LAUNCH_CHECK("eng_m_dssum (outer)");
     eng_m_outer_resid<N><<<g->sms * 4, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ax, G.d_cnt);
     NB_LAUNCH_CHECK("eng_m_outer_resid");
@@ -1153,6 +1168,7 @@ nb_status engine_submit_internal(nb_engine *g, nb_box box, int n, double amp, co
     }
     P.te = te;
     shared_counts(m, P.cx, P.cy, P.cz);
+    P.dd = make_ds_cat(m);
     P.ntile_ax = (int)((m.E + te - 1) / te);
     const int64_t total = (int64_t)P.cx + P.cy + P.cz;
     P.ntile_ds = total > 0 ? (int)((total + kDsTile - 1) / kDsTile) : 1;

@@ -11,32 +11,33 @@
 #include <type_traits>
 
 #include "df.cuh"
+#include "gs_fast.cuh"
 #include "gs_nodes.cuh"
 #include "internal.cuh"
 #include "reduce.cuh"
 
 namespace nekgb {
 
-// Plain dssum (CG = false) or the fused solver step (CG = true): the node
+// Plain dssum (CG = false) or the fused solver step (CG = true), over the
+// shared nodes grouped by category (faces, edges, vertices; DsCat): the node
 // sums are written back and, in the solver, each shared node adds
 // w_g * sum_copies(p)/multiplicity to <w,p>_c; the last CTA adds the
 // element-interior partials left by ax_e, forms alpha = rho/<w,p>_c and
-// flags a breakdown.
-template <typename T, bool CG>
-__global__ void dssum_kernel(T *__restrict__ w, const T *__restrict__ p, Mesh m, int cx,
-                             int cy, int cz, CgScalars *sc, double *partials, int slot0) {
+// flags a breakdown.  N is the number of points per direction.
+template <typename T, bool CG, int N>
+__global__ void __launch_bounds__(256, 5)
+dssum_kernel(T *__restrict__ w, const T *__restrict__ p, DsCat dd, CgScalars *sc, double *partials,
+             int slot0) {
     if (sc && sc->done) return;
-    const int total = cx + cy + cz;
+    const int total = dd.o[7];
     // <w,p>_c share: FP64 for FP64 fields; compensated FP32 (exact products,
     // compensated sums: FP64-class accuracy on the FP32 pipe) for FP32 fields
     constexpr bool F32 = std::is_same<T, float>::value;
     double dot = 0.0;
     dfa::Acc32 dot32;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
-        int gx, gy, gz;
-        shared_node(q, m, cx, cy, gx, gy, gz);
         int64_t idx[8];
-        const int c = node_copies(gx, gy, gz, m, idx);
+        const int c = cat_copies<N>(q, dd, idx);
         // Sum from +0.0 in ascending element order.  (+0.0) + v equals v
         // except for v = -0.0, so the first add is a sign fix-up done with
         // integer operations; the remaining adds are exact-count loops so no
@@ -211,12 +212,27 @@ static int sm_count() {
 }
 
 
-// Eight CTAs per SM striding over the shared nodes (one block reduction
-// per CTA in the solver step).
+// One wave of CTAs (five per SM, the kernel's register bound) striding over
+// the shared nodes (one block reduction per CTA in the solver step).
 int dssum_grid(const nb_ctx *c) {
     int cx, cy, cz;
     shared_counts(c->m, cx, cy, cz);
-    return grid_blocks((int64_t)cx + cy + cz, 256, sm_count() * 8);
+    return grid_blocks((int64_t)cx + cy + cz, 256, sm_count() * 5);
+}
+
+template <typename T, bool CG>
+static void dssum_launch(nb_ctx *c, T *w, const T *p, CgScalars *sc, double *partials, int slot0) {
+    const DsCat dd = make_ds_cat(c->m);
+    const int grid = dssum_grid(c);
+    switch (c->m.n) {
+#define NB_CASE(NN) \
+    case NN: dssum_kernel<T, CG, NN><<<grid, 256, 0, c->stream>>>(w, p, dd, sc, partials, slot0); break;
+        NB_CASE(2) NB_CASE(3) NB_CASE(4) NB_CASE(5) NB_CASE(6) NB_CASE(7) NB_CASE(8)
+        NB_CASE(9) NB_CASE(10) NB_CASE(11) NB_CASE(12) NB_CASE(13) NB_CASE(14) NB_CASE(15)
+        NB_CASE(16)
+#undef NB_CASE
+        default: break;
+    }
 }
 
 nb_status launch_dssum_sc(nb_ctx *c, double *w, const CgScalars *sc) {
@@ -224,19 +240,15 @@ nb_status launch_dssum_sc(nb_ctx *c, double *w, const CgScalars *sc) {
     shared_counts(c->m, cx, cy, cz);
     if ((int64_t)cx + cy + cz == 0) return NB_OK;
     LaunchTimer tm(c, NB_K_DSSUM);
-    dssum_kernel<double, false><<<dssum_grid(c), 256, 0, c->stream>>>(
-        w, nullptr, c->m, cx, cy, cz, const_cast<CgScalars *>(sc), nullptr, 0);
+    dssum_launch<double, false>(c, w, nullptr, const_cast<CgScalars *>(sc), nullptr, 0);
     NB_LAUNCH_CHECK("dssum_kernel");
     return NB_OK;
 }
 
 // Fused solver step: dssum of w, shared-node part of <w,p>_c, alpha.
 nb_status launch_dssum_cg(nb_ctx *c) {
-    int cx, cy, cz;
-    shared_counts(c->m, cx, cy, cz);
     LaunchTimer tm(c, NB_K_DSSUM);
-    dssum_kernel<double, true><<<dssum_grid(c), 256, 0, c->stream>>>(c->d_w, c->d_p, c->m, cx, cy, cz,
-                                                                     c->d_sc, c->d_partials, c->ax_grid);
+    dssum_launch<double, true>(c, c->d_w, c->d_p, c->d_sc, c->d_partials, c->ax_grid);
     NB_LAUNCH_CHECK("dssum_kernel<cg>");
     return NB_OK;
 }
@@ -244,11 +256,8 @@ nb_status launch_dssum_cg(nb_ctx *c) {
 // The same fused step for the FP32 inner solve of the mixed-precision path:
 // node sums in FP32 (ascending element order), <w,p>_c in FP64.
 nb_status launch_dssum_cg32(nb_ctx *c) {
-    int cx, cy, cz;
-    shared_counts(c->m, cx, cy, cz);
     LaunchTimer tm(c, NB_K_DSSUM);
-    dssum_kernel<float, true><<<dssum_grid(c), 256, 0, c->stream>>>(c->d_w32, c->d_p32, c->m, cx, cy, cz,
-                                                                    c->d_sc, c->d_partials, c->ax_grid);
+    dssum_launch<float, true>(c, c->d_w32, c->d_p32, c->d_sc, c->d_partials, c->ax_grid);
     NB_LAUNCH_CHECK("dssum_kernel<f32,cg>");
     return NB_OK;
 }
@@ -259,8 +268,7 @@ nb_status launch_dssum32(nb_ctx *c, float *w) {
     shared_counts(c->m, cx, cy, cz);
     if ((int64_t)cx + cy + cz == 0) return NB_OK;
     LaunchTimer tm(c, NB_K_DSSUM);
-    dssum_kernel<float, false><<<dssum_grid(c), 256, 0, c->stream>>>(w, nullptr, c->m, cx, cy, cz,
-                                                                     nullptr, nullptr, 0);
+    dssum_launch<float, false>(c, w, nullptr, nullptr, nullptr, 0);
     NB_LAUNCH_CHECK("dssum_kernel<f32>");
     return NB_OK;
 }

@@ -1,0 +1,282 @@
+// Shared-node enumeration of the structured box with the polynomial order
+// known at compile time and the mesh-dependent divisors replaced by exact
+// multiply-high reciprocals (Granlund and Montgomery, 1994: for d >= 2,
+// m = ceil(2^64 / d) gives floor(q / d) = floor(q m / 2^64) for every
+// 32-bit q, because q (m d - 2^64) < 2^64).  Same node order and copy
+// order as gs_nodes.cuh, so the sums are bit-identical.
+#pragma once
+
+#include "gs_nodes.cuh"
+#include "internal.cuh"
+
+namespace nekgb {
+
+struct FastDiv {
+    unsigned long long m = 0;
+    unsigned d = 1;
+    static FastDiv make(unsigned d) {
+        FastDiv f;
+        f.d = d;
+        f.m = d <= 1 ? 0ull : (~0ull / d) + 1ull;
+        return f;
+    }
+    __device__ __forceinline__ unsigned div(unsigned q) const {
+        return d <= 1 ? q : (unsigned)__umul64hi((unsigned long long)q, m);
+    }
+};
+
+// Everything the node decode needs about one box mesh.
+struct DsDecode {
+    int cx, cy, cz;                 // shared nodes on x-planes, y-planes (off x), z-planes (off x, y)
+    int ex, ey, ez;                 // elements per direction
+    int NX, NY, NZ, NXp, NYp;       // global nodes per direction; non-plane counts in x and y
+    FastDiv fNY, fNZ, fNXp, fNYp;
+};
+
+inline DsDecode make_ds_decode(const Mesh &m) {
+    DsDecode d;
+    shared_counts(m, d.cx, d.cy, d.cz);
+    d.ex = m.ex; d.ey = m.ey; d.ez = m.ez;
+    d.NX = (int)m.NX; d.NY = (int)m.NY; d.NZ = (int)m.NZ;
+    d.NXp = (int)(m.NX - (m.ex - 1));
+    d.NYp = (int)(m.NY - (m.ey - 1));
+    d.fNY = FastDiv::make((unsigned)d.NY);
+    d.fNZ = FastDiv::make((unsigned)d.NZ);
+    d.fNXp = FastDiv::make((unsigned)d.NXp);
+    d.fNYp = FastDiv::make((unsigned)d.NYp);
+    return d;
+}
+
+// Non-plane coordinate q (of NG - (ne - 1)) -> global coordinate.
+template <int N>
+__device__ __forceinline__ int nonplane_coord_n(int q, int ne, int NG) {
+    if (q == 0) return 0;
+    if (q == ne * (N - 2) + 1) return NG - 1;
+    if constexpr (N > 2) {
+        const int qq = q - 1;
+        return (qq / (N - 2)) * (N - 1) + 1 + qq % (N - 2);
+    }
+    return 0;
+}
+
+template <int N>
+__device__ __forceinline__ void shared_node_n(int q, const DsDecode &d, int &gx, int &gy, int &gz) {
+    constexpr int N1 = N - 1;
+    if (q < d.cx) {
+        unsigned r = (unsigned)q, t = d.fNY.div(r);
+        gy = (int)(r - t * (unsigned)d.NY);
+        r = t;
+        t = d.fNZ.div(r);
+        gz = (int)(r - t * (unsigned)d.NZ);
+        gx = (int)(t + 1) * N1;
+    } else if (q < d.cx + d.cy) {
+        unsigned r = (unsigned)(q - d.cx), t = d.fNXp.div(r);
+        gx = nonplane_coord_n<N>((int)(r - t * (unsigned)d.NXp), d.ex, d.NX);
+        r = t;
+        t = d.fNZ.div(r);
+        gz = (int)(r - t * (unsigned)d.NZ);
+        gy = (int)(t + 1) * N1;
+    } else {
+        unsigned r = (unsigned)(q - d.cx - d.cy), t = d.fNXp.div(r);
+        gx = nonplane_coord_n<N>((int)(r - t * (unsigned)d.NXp), d.ex, d.NX);
+        r = t;
+        t = d.fNYp.div(r);
+        gy = nonplane_coord_n<N>((int)(r - t * (unsigned)d.NYp), d.ey, d.NY);
+        gz = (int)(t + 1) * N1;
+    }
+}
+
+// Copies of global coordinate g along one direction (ascending element).
+template <int N>
+__device__ __forceinline__ int copies_1d_n(int g, int ne, int *el, int *li) {
+    constexpr int N1 = N - 1;
+    const int a = g / N1;
+    const int rem = g - a * N1;
+    if (rem == 0 && a > 0 && a < ne) {
+        el[0] = a - 1; li[0] = N1;
+        el[1] = a;     li[1] = 0;
+        return 2;
+    }
+    const int ee = a < ne ? a : ne - 1;
+    el[0] = ee;
+    li[0] = g - ee * N1;
+    return 1;
+}
+
+// Local indices of the copies of node (gx, gy, gz), ascending element order.
+template <int N>
+__device__ __forceinline__ int node_copies_n(int gx, int gy, int gz, const DsDecode &d, int64_t *idx) {
+    constexpr int64_t N3 = (int64_t)N * N * N;
+    int elx[2], lix[2], ely[2], liy[2], elz[2], liz[2];
+    const int nx = copies_1d_n<N>(gx, d.ex, elx, lix);
+    const int ny = copies_1d_n<N>(gy, d.ey, ely, liy);
+    const int nz = copies_1d_n<N>(gz, d.ez, elz, liz);
+    int c = 0;
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        if (a >= nz) break;
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            if (b >= ny) break;
+#pragma unroll
+            for (int x = 0; x < 2; x++) {
+                if (x >= nx) break;
+                const int64_t e = elx[x] + (int64_t)d.ex * (ely[b] + (int64_t)d.ey * elz[a]);
+                idx[c++] = e * N3 + lix[x] + N * (liy[b] + N * liz[a]);
+            }
+        }
+    }
+    return c;
+}
+
+}  // namespace nekgb
+
+namespace nekgb {
+
+// ---------------------------------------------------------------- by category
+// The shared nodes grouped by how many coordinates lie on an interior
+// element interface: face nodes (one; 2 copies), edge nodes (two; 4 copies)
+// and vertices (three; 8 copies).  Within a category every node has the
+// same copy count and the copies sit at fixed offsets from the first, so a
+// warp runs one branch-free path.  Non-interface coordinates are counted in
+// "non-plane" indices (box-boundary nodes and element-interior nodes).
+struct DsCat {
+    int ex, ey, ez;
+    int NXp, NYp, NZp;              // non-plane coordinate counts per direction
+    int o[8];                        // range starts: Fx, Fy, Fz, Exy, Exz, Eyz, V, end
+    FastDiv fNXp, fNYp, fNZp, fEx1, fEy1;
+};
+
+inline DsCat make_ds_cat(const Mesh &m) {
+    DsCat d;
+    d.ex = m.ex; d.ey = m.ey; d.ez = m.ez;
+    d.NXp = (int)(m.NX - (m.ex - 1));
+    d.NYp = (int)(m.NY - (m.ey - 1));
+    d.NZp = (int)(m.NZ - (m.ez - 1));
+    const int64_t ax = m.ex - 1, ay = m.ey - 1, az = m.ez - 1;
+    const int64_t cnt[7] = {ax * d.NYp * d.NZp, ay * d.NXp * d.NZp, az * d.NXp * d.NYp,
+                            ax * ay * d.NZp,    ax * az * d.NYp,    ay * az * d.NXp,
+                            ax * ay * az};
+    d.o[0] = 0;
+    for (int k = 0; k < 7; k++) d.o[k + 1] = d.o[k] + (int)cnt[k];
+    d.fNXp = FastDiv::make((unsigned)d.NXp);
+    d.fNYp = FastDiv::make((unsigned)d.NYp);
+    d.fNZp = FastDiv::make((unsigned)d.NZp);
+    d.fEx1 = FastDiv::make((unsigned)(ax > 0 ? ax : 1));
+    d.fEy1 = FastDiv::make((unsigned)(ay > 0 ? ay : 1));
+    return d;
+}
+
+// Non-plane index g (of ne (N-2) + 2) -> (element, local index) along one
+// direction: 0 -> (0, 0), the last -> (ne - 1, N - 1), others are
+// element-interior points.
+template <int N>
+__device__ __forceinline__ void nonplane_elem(int g, int ne, int &el, int &li) {
+    if (g == 0) { el = 0; li = 0; return; }
+    if (g == ne * (N - 2) + 1) { el = ne - 1; li = N - 1; return; }
+    if constexpr (N > 2) {
+        const int qq = g - 1;
+        el = qq / (N - 2);
+        li = 1 + qq % (N - 2);
+    } else {
+        el = 0; li = 0;
+    }
+}
+
+__device__ __forceinline__ void divmod(unsigned q, const FastDiv &f, unsigned &quo, unsigned &rem) {
+    quo = f.div(q);
+    rem = q - quo * f.d;
+}
+
+// Copies of shared node q (a global enumeration over the seven ranges of
+// DsCat) in ascending element order; returns the copy count (2, 4 or 8).
+template <int N>
+__device__ __forceinline__ int cat_copies(int q, const DsCat &d, int64_t *idx) {
+    constexpr int N1 = N - 1, N2 = N * N;
+    constexpr int64_t N3 = (int64_t)N * N * N;
+    const int64_t sy = d.ex, sz = (int64_t)d.ex * d.ey;   // element id strides
+    unsigned t, r0, r1;
+    int ex, ey, ez, lx, ly, lz;
+    if (q < d.o[3]) {                         // face nodes: 2 copies
+        if (q < d.o[1]) {                     // x-interface a+1 between elements a and a+1
+            divmod((unsigned)q, d.fNYp, t, r0);
+            divmod(t, d.fNZp, t, r1);
+            nonplane_elem<N>((int)r0, d.ey, ey, ly);
+            nonplane_elem<N>((int)r1, d.ez, ez, lz);
+            const int64_t e = (int64_t)t + sy * ey + sz * ez;
+            idx[0] = e * N3 + N1 + N * ly + N2 * lz;
+            idx[1] = idx[0] + N3 - N1;
+        } else if (q < d.o[2]) {              // y-interface
+            divmod((unsigned)(q - d.o[1]), d.fNXp, t, r0);
+            divmod(t, d.fNZp, t, r1);
+            nonplane_elem<N>((int)r0, d.ex, ex, lx);
+            nonplane_elem<N>((int)r1, d.ez, ez, lz);
+            const int64_t e = ex + sy * (int64_t)t + sz * ez;
+            idx[0] = e * N3 + lx + N * N1 + N2 * lz;
+            idx[1] = idx[0] + sy * N3 - N * N1;
+        } else {                              // z-interface
+            divmod((unsigned)(q - d.o[2]), d.fNXp, t, r0);
+            divmod(t, d.fNYp, t, r1);
+            nonplane_elem<N>((int)r0, d.ex, ex, lx);
+            nonplane_elem<N>((int)r1, d.ey, ey, ly);
+            const int64_t e = ex + sy * ey + sz * (int64_t)t;
+            idx[0] = e * N3 + lx + N * ly + N2 * N1;
+            idx[1] = idx[0] + sz * N3 - N2 * N1;
+        }
+        return 2;
+    }
+    if (q < d.o[6]) {                         // edge nodes: 4 copies
+        int64_t e, s1, s2;
+        int l0;
+        if (q < d.o[4]) {                     // x- and y-interfaces, along z
+            divmod((unsigned)(q - d.o[3]), d.fNZp, t, r0);
+            divmod(t, d.fEx1, t, r1);         // r1 = a, t = b
+            nonplane_elem<N>((int)r0, d.ez, ez, lz);
+            e = (int64_t)r1 + sy * (int64_t)t + sz * ez;
+            l0 = N1 + N * N1 + N2 * lz;
+            s1 = 1; s2 = sy;
+            idx[0] = e * N3 + l0;
+            idx[1] = (e + s1) * N3 + l0 - N1;
+            idx[2] = (e + s2) * N3 + l0 - N * N1;
+            idx[3] = (e + s1 + s2) * N3 + l0 - N1 - N * N1;
+        } else if (q < d.o[5]) {              // x- and z-interfaces, along y
+            divmod((unsigned)(q - d.o[4]), d.fNYp, t, r0);
+            divmod(t, d.fEx1, t, r1);         // r1 = a, t = c
+            nonplane_elem<N>((int)r0, d.ey, ey, ly);
+            e = (int64_t)r1 + sy * ey + sz * (int64_t)t;
+            l0 = N1 + N * ly + N2 * N1;
+            s1 = 1; s2 = sz;
+            idx[0] = e * N3 + l0;
+            idx[1] = (e + s1) * N3 + l0 - N1;
+            idx[2] = (e + s2) * N3 + l0 - N2 * N1;
+            idx[3] = (e + s1 + s2) * N3 + l0 - N1 - N2 * N1;
+        } else {                              // y- and z-interfaces, along x
+            divmod((unsigned)(q - d.o[5]), d.fNXp, t, r0);
+            divmod(t, d.fEy1, t, r1);         // r1 = b, t = c
+            nonplane_elem<N>((int)r0, d.ex, ex, lx);
+            e = ex + sy * (int64_t)r1 + sz * (int64_t)t;
+            l0 = lx + N * N1 + N2 * N1;
+            s1 = sy; s2 = sz;
+            idx[0] = e * N3 + l0;
+            idx[1] = (e + s1) * N3 + l0 - N * N1;
+            idx[2] = (e + s2) * N3 + l0 - N2 * N1;
+            idx[3] = (e + s1 + s2) * N3 + l0 - N * N1 - N2 * N1;
+        }
+        return 4;
+    }
+    // vertices: 8 copies, z outer, y, x inner
+    divmod((unsigned)(q - d.o[6]), d.fEx1, t, r0);   // r0 = a
+    divmod(t, d.fEy1, t, r1);                          // r1 = b, t = c
+    const int64_t e = (int64_t)r0 + sy * (int64_t)r1 + sz * (int64_t)t;
+#pragma unroll
+    for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+        for (int dy = 0; dy < 2; dy++)
+#pragma unroll
+            for (int dx = 0; dx < 2; dx++)
+                idx[dz * 4 + dy * 2 + dx] = (e + dx + sy * dy + sz * dz) * N3 + (dx ? 0 : N1) +
+                                            N * (dy ? 0 : N1) + N2 * (dz ? 0 : N1);
+    return 8;
+}
+
+}  // namespace nekgb

@@ -98,19 +98,28 @@ __global__ void __launch_bounds__(kT)
 inner_update_kernel(float *__restrict__ r, const float *__restrict__ w, Mesh m, double *partials,
                     CgScalars *sc) {
     constexpr int N3 = N * N * N;
+    constexpr int K = (N3 + kT - 1) / kT;   // points per thread per element
     if (sc->done) return;
     const float alpha = (float)sc->alpha;
     dfa::Acc32 acc;   // exact products, compensated sums (FP64-class <r,r>_c)
+    unsigned pf[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const int q = threadIdx.x + k * kT;
+        pf[k] = q < N3 ? point_faces<N>(q) : 0u;
+    }
     for (int64_t e = blockIdx.x; e < m.E; e += gridDim.x) {
         int ex, ey, ez;
         element_coords(e, m, ex, ey, ez);
+        const unsigned sf = shared_faces(ex, ey, ez, m);
         const int64_t base = e * N3;
-#pragma unroll 4
-        for (int q = threadIdx.x; q < N3; q += kT) {
-            const int i = q % N, j = (q / N) % N, k = q / (N * N);
-            const float rn = fmaf(-alpha, w[base + q], r[base + q]);
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const int q = threadIdx.x + k * kT;
+            if (K * kT != N3 && q >= N3) break;
+            const float rn = fmaf(-alpha, __ldcs(w + base + q), r[base + q]);
             r[base + q] = rn;
-            const float cw = __uint_as_float((unsigned)(127 - log2_mult(i, j, k, ex, ey, ez, m)) << 23);  // 2^-lg
+            const float cw = __uint_as_float((127u - __popc(pf[k] & sf)) << 23);  // 2^-lg
             acc.add_prod(rn * cw, rn);
         }
     }

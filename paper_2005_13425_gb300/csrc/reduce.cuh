@@ -90,6 +90,22 @@ __device__ __forceinline__ bool on_box_face(int i, int j, int k, int ex, int ey,
            (j == n - 1 && ey == m.ey - 1) || (k == 0 && ez == 0) || (k == n - 1 && ez == m.ez - 1);
 }
 
+// Faces of the element that local point q lies on, as bits: i = 0, i = n-1,
+// j = 0, j = n-1, k = 0, k = n-1.
+template <int N>
+__device__ __forceinline__ unsigned point_faces(int q) {
+    const int i = q % N, j = (q / N) % N, k = q / (N * N);
+    return (unsigned)(i == 0) | ((unsigned)(i == N - 1) << 1) | ((unsigned)(j == 0) << 2) |
+           ((unsigned)(j == N - 1) << 3) | ((unsigned)(k == 0) << 4) | ((unsigned)(k == N - 1) << 5);
+}
+
+// Faces of element (ex,ey,ez) shared with a neighbour, in point_faces' bit
+// order: log2 of a point's multiplicity is popc(point_faces & shared_faces).
+__device__ __forceinline__ unsigned shared_faces(int ex, int ey, int ez, const Mesh &m) {
+    return (unsigned)(ex > 0) | ((unsigned)(ex < m.ex - 1) << 1) | ((unsigned)(ey > 0) << 2) |
+           ((unsigned)(ey < m.ey - 1) << 3) | ((unsigned)(ez > 0) << 4) | ((unsigned)(ez < m.ez - 1) << 5);
+}
+
 // Element id -> (ex, ey, ez) with 32-bit arithmetic.
 __device__ __forceinline__ void element_coords(int64_t e, const Mesh &m, int &ex, int &ey, int &ez) {
     const int ei = (int)e;

@@ -2,7 +2,11 @@
 
 Tolerances: the inverse diagonal agrees to 1e-13 relative (same formula,
 different rounding order); PCG histories and iterates to 1e-8 after 50 fixed
-iterations, as for plain CG.
+iterations, as for plain CG.  Iteration counts to a tolerance agree within
+1 % of the oracle's (at least 2): the device's reductions sum in another
+order than the oracle's sequential loop, and on these deliberately
+ill-conditioned problems (element scales spread over e^+-3) CG turns such
+rounding differences into a few iterations more or fewer.
 """
 import numpy as np
 import pytest
@@ -32,6 +36,10 @@ def dev(a):
 def host(t):
     torch.cuda.current_stream().synchronize()
     return t.cpu().numpy()
+
+
+def its_tol(it_ref):
+    return max(2, int(0.01 * it_ref))
 
 
 def stretched(oracle, dims, n, seed=2):
@@ -78,12 +86,12 @@ def test_jacobi_pcg_converges_faster_and_switches_off(nek, oracle):
         nek.nb_set_preconditioner(h, 1)
         x = torch.zeros_like(dev(f))
         st, it_p, rr = nek.nb_cg_solve(h, dev(f), x, tol=1e-10, maxit=20000)
-        assert rr <= 1e-10 and abs(it_p - it_p_ref) <= 2 and it_p < it_c_ref
+        assert rr <= 1e-10 and abs(it_p - it_p_ref) <= its_tol(it_p_ref) and it_p < it_c_ref
         xp = host(x)
         nek.nb_set_preconditioner(h, 0)                    # back to the paper's plain CG
         x.zero_()
         st, it_c, rr = nek.nb_cg_solve(h, dev(f), x, tol=1e-10, maxit=20000)
-        assert abs(it_c - it_c_ref) <= 2
+        assert abs(it_c - it_c_ref) <= its_tol(it_c_ref)
         assert np.abs(host(x) - xp).max() <= 1e-7 * np.abs(xp).max()
     finally:
         nek.nb_destroy(h)
