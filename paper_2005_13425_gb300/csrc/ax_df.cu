@@ -38,7 +38,7 @@ struct AxDfArgs {
     const double *minv;   // MODE 1: Jacobi inverse diagonal or null
     const CgScalars *sc;  // MODE 1
     double *partials;     // MODE 1 fused: one <w,p> partial per CTA
-    int fuse;             // MODE 1: zero box-face points, interior <w,p>
+    int fuse;             // MODE 1: zero box-face points, local products w p
     Mesh m;
     const float2 *g;      // gxyz pairs [E][6][n^3], scaled by 2^-(gexp-1023)
     int gexp;             // biased exponent of max|gxyz|

@@ -183,8 +183,8 @@ __device__ __forceinline__ unsigned box_faces(int ex, int ey, int ez, const Mesh
 // (every thread must call it; it contains barriers).  sm holds 6 n^3 pairs,
 // s_emax is a shared int that must be 0 on entry (left 0 on exit).
 // MODE 1 is the CG head: x += xa p, p = r + beta p, w = ax_e(p); with fuse,
-// box-face points of w are zeroed and the element-interior <w,p> is added
-// to dot; pf holds the thread's point-face masks (df_point_masks; null:
+// box-face points of w are zeroed and the element's share of <w,p>_c (the
+// local products, see the final loop) is added to dot; pf holds the thread's point-face masks (df_point_masks; null:
 // computed per point) and (ex, ey, ez) is the element's position in the box m.  The geometric
 // factors and x are loaded with the streaming (evict-first) cache policy:
 // they are not read again in the iteration, which keeps w and p in L2 for
@@ -299,8 +299,9 @@ __device__ __forceinline__ void df_element(const DfElemIO &io, double beta, doub
     // ---- w = r-partial + s-partial + t-partial, scaled back, FP64 out
     if (MODE == 1 && fuse) {
         // Dirichlet points are zeroed before dssum (their sum is then +0, as
-        // mask-after-dssum gives); element-interior points (no face bit)
-        // have multiplicity 1 and are final: <w,p> here.
+        // mask-after-dssum gives).  <w,p>_c is summed here over all local
+        // points: p is continuous, so sum_g (sum_copies w) p_g equals the
+        // sum of the local products before assembly.
         const unsigned bf = box_faces(ex, ey, ez, m);
 #pragma unroll
         for (int k = 0; k < df_points_per_thread<N, T>(); k++) {
@@ -311,7 +312,7 @@ __device__ __forceinline__ void df_element(const DfElemIO &io, double beta, doub
             const unsigned f = pf ? pf[k] : point_faces<N>(q);
             if (f & bf)
                 wv = 0.0;
-            else if (f == 0u)
+            else
                 dot = fma(wv, io.p[q], dot);
             io.w[q] = wv;
         }

@@ -71,7 +71,8 @@ struct F32ElemIO {
 // One element, executed by the whole CTA of T threads (contains barriers;
 // every thread must call it).  MODE 0: w = ax_e(u).  MODE 1: the inner CG
 // head, x += xa p, p = r + beta p, w = ax_e(p) with box-face points zeroed
-// and the element-interior <w,p> added to dot.  (ex, ey, ez) is the
+// and the local products w p added to dot (their sum over all elements is
+// <w,p>_c after assembly, because p is continuous).  (ex, ey, ez) is the
 // element's position in the box m.
 template <int N, int MODE, int T>
 __device__ __forceinline__ void f32_element(const F32ElemIO &io, float beta, float xa, int ex, int ey, int ez,
@@ -157,7 +158,7 @@ __device__ __forceinline__ void f32_element(const F32ElemIO &io, float beta, flo
             const int i = q % N, j = (q / N) % N, k = q / N2;
             if (on_box_face(i, j, k, ex, ey, ez, m))
                 wv = 0.f;
-            else if (i > 0 && i < N - 1 && j > 0 && j < N - 1 && k > 0 && k < N - 1)
+            else
                 dot.add_prod(wv, io.p[q]);
         }
         io.w[q] = wv;
@@ -277,7 +278,7 @@ __device__ __forceinline__ void f32_element_staged(float *st, float *W, const F3
             const int i = q % N, j = (q / N) % N, k = q / N2;
             if (on_box_face(i, j, k, ex, ey, ez, m))
                 wv = 0.f;
-            else if (i > 0 && i < N - 1 && j > 0 && j < N - 1 && k > 0 && k < N - 1)
+            else
                 dot.add_prod(wv, U[q]);
         }
         o.w[q] = wv;

@@ -34,14 +34,15 @@ struct AxCgArgs {
     const double *minv;   // Jacobi inverse diagonal (z = minv r) or null
     const CgScalars *sc;
     double *partials;     // fused: one <w,p> partial per CTA
-    int fuse;             // zero box-face points and sum <w,p> over interior points
+    int fuse;             // zero box-face points and sum the local products w p
     Mesh m;
 };
 
 // MODE 0: w = ax_e(u).
 // MODE 1: CG iteration head: x += x_alpha p, p = r + beta p (written back),
 //         w = ax_e(p); when fused, box-face points of w are zeroed and the
-//         element-interior part of <w,p> is reduced per CTA.
+//         local products w p (whose sum is <w,p>_c after assembly, p being
+//         continuous) are reduced per CTA.
 template <int N, int MODE>
 __global__ void __launch_bounds__(((N * N + 31) / 32) * 32)
 ax_fp64_kernel(const double *__restrict__ u, double *__restrict__ w,
@@ -134,7 +135,7 @@ ax_fp64_kernel(const double *__restrict__ u, double *__restrict__ w,
                 if (MODE == 1 && cg.fuse) {
                     if (on_box_face(i, j, m, ex, ey, ez, cg.m))
                         wv = 0.0;
-                    else if (i > 0 && i < N - 1 && j > 0 && j < N - 1 && m > 0 && m < N - 1)
+                    else
                         dot = fma(wv, cg.p[base + i + N * (j + N * m)], dot);
                 }
                 w[base + i + N * (j + N * m)] = wv;

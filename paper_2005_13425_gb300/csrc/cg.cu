@@ -8,9 +8,9 @@
 // one iteration is three kernels:
 //   1. ax_e head: x += alpha_prev p (the x update owed by the previous
 //      iteration), p = r + beta p, w = ax_e(p), w := 0 on box faces, and
-//      the element-interior part of <w,p>_c;
-//   2. dssum of w with the shared-node part of <w,p>_c; its last CTA forms
-//      alpha = rho/<w,p>_c;
+//      <w,p>_c as the sum of the local products w p (p is continuous, so
+//      sum_g (sum_copies w) p_g equals the sum over local points);
+//   2. dssum of w; its last CTA forms alpha = rho/<w,p>_c;
 //   3. r -= alpha w with <r,r>_c; its last CTA forms rho, beta and the
 //      convergence decision.
 // The last owed x update runs once after the loop.  With a caller-supplied

@@ -110,8 +110,9 @@ eng_ax_head(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const i
     }
 }
 
-// dssum of w over (slot, node tile) work units, shared-node <w,p>_c, and in
-// the problem's last tile: alpha = rho/<w,p>_c.
+// dssum of w over (slot, node tile) work units; in the problem's last tile:
+// alpha = rho/<w,p>_c from the head's partials (the local products w p,
+// whose sum is the assembled <w,p>_c because p is continuous).
 template <int N>
 __global__ void __launch_bounds__(kEngThreads)
 eng_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles) {
@@ -124,20 +125,14 @@ eng_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int
         if (P.sc.done) continue;
         const int total = P.cx + P.cy + P.cz;
         double *w = P.w;
-        const double *p = P.p;
-        double dot = 0.0;
         const int q0 = tile.y * kDsTile;
         const int q1 = q0 + kDsTile < total ? q0 + kDsTile : total;
         for (int q = q0 + threadIdx.x; q < q1; q += kEngThreads) {
             int64_t idx[8];
             const int c = cat_copies<N>(q, P.dd, idx);
             double s;
-            double ps;
-            int lg;
             if (c == 2) {
                 s = plus_zero(w[idx[0]]) + w[idx[1]];
-                ps = p[idx[0]] + p[idx[1]];
-                lg = 1;
             } else if (c == 4) {
                 double a[4];
 #pragma unroll
@@ -145,10 +140,6 @@ eng_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int
                 s = plus_zero(a[0]);
 #pragma unroll
                 for (int k = 1; k < 4; k++) s = s + a[k];
-                ps = p[idx[0]];
-#pragma unroll
-                for (int k = 1; k < 4; k++) ps += p[idx[k]];
-                lg = 2;
             } else {
                 double a[8];
 #pragma unroll
@@ -156,17 +147,10 @@ eng_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int
                 s = plus_zero(a[0]);
 #pragma unroll
                 for (int k = 1; k < 8; k++) s = s + a[k];
-                ps = p[idx[0]];
-#pragma unroll
-                for (int k = 1; k < 8; k++) ps += p[idx[k]];
-                lg = 3;
             }
             for (int k = 0; k < c; k++) w[idx[k]] = s;
-            dot = node_dot(dot, s, lg, ps);
         }
-        const double b = block_sum(dot, red);
         if (threadIdx.x == 0) {
-            P.partials[P.ntile_ax + tile.y] = b;
             __threadfence();
             const unsigned t = atomicAdd(&P.sc.ticket, 1u);
             s_last = (t == (unsigned)P.ntile_ds - 1);
@@ -175,8 +159,7 @@ eng_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int
         if (s_last) {
             __threadfence();
             double acc = 0.0;
-            const int cnt = P.ntile_ax + P.ntile_ds;
-            for (int k = threadIdx.x; k < cnt; k += kEngThreads) acc += __ldcg(P.partials + k);
+            for (int k = threadIdx.x; k < P.ntile_ax; k += kEngThreads) acc += __ldcg(P.partials + k);
             const double pap = block_sum(acc, red);
             if (threadIdx.x == 0) {
                 P.sc.ticket = 0;
@@ -357,7 +340,7 @@ __global__ void eng_final_x(ProbDesc *__restrict__ desc, int slot) {
 // by the problem's own last tile, so results stay independent of the mix.
 
 // Inner CG head over (slot, tile) work units: z += xa p, p = r + beta p,
-// w = ax_e(p) in FP32, box faces zeroed, element-interior <w,p>_c.
+// w = ax_e(p) in FP32, box faces zeroed, local products w p per tile.
 template <int N, int T>
 __global__ void __launch_bounds__(T)
 eng_m_head(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles,
@@ -395,8 +378,8 @@ eng_m_head(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const in
 }
 
 // Shared-node sums of the FP32 w (and of the FP64 w in the outer pass, DOT
-// = false) over (slot, node tile) work units.  With DOT, the shared-node
-// <w,p>_c is accumulated and the problem's last tile forms alpha.
+// = false) over (slot, node tile) work units.  With DOT, the problem's last
+// tile forms alpha from the head's partials (local products w p).
 template <typename T, bool DOT, int N>
 __global__ void __launch_bounds__(kEngThreads)
 eng_m_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles) {
@@ -413,10 +396,8 @@ eng_m_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const i
         }
         const int total = P.cx + P.cy + P.cz;
         T *w;
-        const float *p = P.p32;
         if constexpr (DOT) w = P.w32;
         else w = P.w;
-        dfa::Acc32 dot;
         const int q0 = tile.y * kDsTile;
         const int q1 = q0 + kDsTile < total ? q0 + kDsTile : total;
         for (int q = q0 + threadIdx.x; q < q1; q += kEngThreads) {
@@ -441,15 +422,9 @@ eng_m_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const i
                 for (int k = 1; k < 8; k++) s = s + a[k];
             }
             for (int k = 0; k < c; k++) w[idx[k]] = s;
-            if constexpr (DOT) {
-                const float sc = s * (c == 2 ? 0.5f : (c == 4 ? 0.25f : 0.125f));
-                for (int k = 0; k < c; k++) dot.add_prod(sc, p[idx[k]]);
-            }
         }
         if constexpr (DOT) {
-            const double b = block_sum(dot.value(), red);
             if (threadIdx.x == 0) {
-                P.partials[P.ntile_ax + tile.y] = b;
                 __threadfence();
                 const unsigned t = atomicAdd(&P.si.ticket, 1u);
                 s_last = (t == (unsigned)P.ntile_ds - 1);
@@ -458,8 +433,7 @@ eng_m_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const i
             if (s_last) {
                 __threadfence();
                 double acc = 0.0;
-                const int cnt = P.ntile_ax + P.ntile_ds;
-                for (int k = threadIdx.x; k < cnt; k += kEngThreads) acc += __ldcg(P.partials + k);
+                for (int k = threadIdx.x; k < P.ntile_ax; k += kEngThreads) acc += __ldcg(P.partials + k);
                 const double pap = block_sum(acc, red);
                 if (threadIdx.x == 0) {
                     P.si.ticket = 0;

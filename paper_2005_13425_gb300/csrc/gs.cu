@@ -19,41 +19,29 @@
 namespace nekgb {
 
 // Plain dssum (CG = false) or the fused solver step (CG = true), over the
-// shared nodes grouped by category (faces, edges, vertices; DsCat): the node
-// sums are written back and, in the solver, each shared node adds
-// w_g * sum_copies(p)/multiplicity to <w,p>_c; the last CTA adds the
-// element-interior partials left by ax_e, forms alpha = rho/<w,p>_c and
-// flags a breakdown.  N is the number of points per direction.
+// shared nodes grouped by category (faces, edges, vertices; DsCat): each
+// node adds its copies from +0.0 in ascending element order and writes the
+// sum back to every copy.  In the solver the ax_e head has already summed
+// <w,p>_c as local products (p is continuous, so the assembled product
+// equals the sum of the unassembled ones); the last CTA here reduces those
+// partials, forms alpha = rho/<w,p>_c and flags a breakdown.  N is the
+// number of points per direction.
 template <typename T, bool CG, int N>
 __global__ void __launch_bounds__(256, 5)
-dssum_kernel(T *__restrict__ w, const T *__restrict__ p, DsCat dd, CgScalars *sc, double *partials,
-             int slot0) {
+dssum_kernel(T *__restrict__ w, DsCat dd, CgScalars *sc, double *partials, int slot0) {
     if (sc && sc->done) return;
     const int total = dd.o[7];
-    // <w,p>_c share: FP64 for FP64 fields; compensated FP32 (exact products,
-    // compensated sums: FP64-class accuracy on the FP32 pipe) for FP32 fields
-    constexpr bool F32 = std::is_same<T, float>::value;
-    double dot = 0.0;
-    dfa::Acc32 dot32;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
         int64_t idx[8];
         const int c = cat_copies<N>(q, dd, idx);
-        // Sum from +0.0 in ascending element order.  (+0.0) + v equals v
-        // except for v = -0.0, so the first add is a sign fix-up done with
-        // integer operations; the remaining adds are exact-count loops so no
-        // predicated-off FP64 adds are issued (GB300's FP64 pipe is narrow).
+        // (+0.0) + v equals v except for v = -0.0, so the first add is a sign
+        // fix-up done with integer operations; the remaining adds are
+        // exact-count loops (no predicated-off FP64 adds on GB300's narrow
+        // FP64 pipe).
         if (c == 2) {
-            const T a0 = w[idx[0]], a1 = w[idx[1]];
-            const T s = plus_zero(a0) + a1;
+            const T s = plus_zero(w[idx[0]]) + w[idx[1]];
             w[idx[0]] = s;
             w[idx[1]] = s;
-            if constexpr (CG && F32) {
-                const float sc = s * 0.5f;
-                dot32.add_prod(sc, p[idx[0]]);
-                dot32.add_prod(sc, p[idx[1]]);
-            } else if constexpr (CG) {
-                dot = node_dot(dot, s, 1, (double)p[idx[0]] + (double)p[idx[1]]);
-            }
         } else if (c == 4) {
             T a[4];
 #pragma unroll
@@ -63,16 +51,6 @@ dssum_kernel(T *__restrict__ w, const T *__restrict__ p, DsCat dd, CgScalars *sc
             for (int k = 1; k < 4; k++) s = s + a[k];
 #pragma unroll
             for (int k = 0; k < 4; k++) w[idx[k]] = s;
-            if constexpr (CG && F32) {
-                const float sc = s * 0.25f;
-#pragma unroll
-                for (int k = 0; k < 4; k++) dot32.add_prod(sc, p[idx[k]]);
-            } else if constexpr (CG) {
-                double ps = (double)p[idx[0]];
-#pragma unroll
-                for (int k = 1; k < 4; k++) ps += (double)p[idx[k]];
-                dot = node_dot(dot, s, 2, ps);
-            }
         } else {
             T a[8];
 #pragma unroll
@@ -82,21 +60,10 @@ dssum_kernel(T *__restrict__ w, const T *__restrict__ p, DsCat dd, CgScalars *sc
             for (int k = 1; k < 8; k++) s = s + a[k];
 #pragma unroll
             for (int k = 0; k < 8; k++) w[idx[k]] = s;
-            if constexpr (CG && F32) {
-                const float sc = s * 0.125f;
-#pragma unroll
-                for (int k = 0; k < 8; k++) dot32.add_prod(sc, p[idx[k]]);
-            } else if constexpr (CG) {
-                double ps = (double)p[idx[0]];
-#pragma unroll
-                for (int k = 1; k < 8; k++) ps += (double)p[idx[k]];
-                dot = node_dot(dot, s, 3, ps);
-            }
         }
     }
-    if constexpr (F32) dot += dot32.value();
     if (CG) {
-        double v[1] = {dot}, tot[1];
+        double v[1] = {0.0}, tot[1];
         if (!last_block_reduce<1>(v, partials, 0, slot0 + blockIdx.x, slot0 + gridDim.x, gridDim.x,
                                   &sc->ticket, tot))
             return;
@@ -221,12 +188,12 @@ int dssum_grid(const nb_ctx *c) {
 }
 
 template <typename T, bool CG>
-static void dssum_launch(nb_ctx *c, T *w, const T *p, CgScalars *sc, double *partials, int slot0) {
+static void dssum_launch(nb_ctx *c, T *w, CgScalars *sc, double *partials, int slot0) {
     const DsCat dd = make_ds_cat(c->m);
     const int grid = dssum_grid(c);
     switch (c->m.n) {
 #define NB_CASE(NN) \
-    case NN: dssum_kernel<T, CG, NN><<<grid, 256, 0, c->stream>>>(w, p, dd, sc, partials, slot0); break;
+    case NN: dssum_kernel<T, CG, NN><<<grid, 256, 0, c->stream>>>(w, dd, sc, partials, slot0); break;
         NB_CASE(2) NB_CASE(3) NB_CASE(4) NB_CASE(5) NB_CASE(6) NB_CASE(7) NB_CASE(8)
         NB_CASE(9) NB_CASE(10) NB_CASE(11) NB_CASE(12) NB_CASE(13) NB_CASE(14) NB_CASE(15)
         NB_CASE(16)
@@ -240,24 +207,24 @@ nb_status launch_dssum_sc(nb_ctx *c, double *w, const CgScalars *sc) {
     shared_counts(c->m, cx, cy, cz);
     if ((int64_t)cx + cy + cz == 0) return NB_OK;
     LaunchTimer tm(c, NB_K_DSSUM);
-    dssum_launch<double, false>(c, w, nullptr, const_cast<CgScalars *>(sc), nullptr, 0);
+    dssum_launch<double, false>(c, w, const_cast<CgScalars *>(sc), nullptr, 0);
     NB_LAUNCH_CHECK("dssum_kernel");
     return NB_OK;
 }
 
-// Fused solver step: dssum of w, shared-node part of <w,p>_c, alpha.
+// Fused solver step: dssum of w and alpha = rho/<w,p>_c.
 nb_status launch_dssum_cg(nb_ctx *c) {
     LaunchTimer tm(c, NB_K_DSSUM);
-    dssum_launch<double, true>(c, c->d_w, c->d_p, c->d_sc, c->d_partials, c->ax_grid);
+    dssum_launch<double, true>(c, c->d_w, c->d_sc, c->d_partials, c->ax_grid);
     NB_LAUNCH_CHECK("dssum_kernel<cg>");
     return NB_OK;
 }
 
 // The same fused step for the FP32 inner solve of the mixed-precision path:
-// node sums in FP32 (ascending element order), <w,p>_c in FP64.
+// node sums in FP32 (ascending element order); <w,p>_c (from the head) in FP64.
 nb_status launch_dssum_cg32(nb_ctx *c) {
     LaunchTimer tm(c, NB_K_DSSUM);
-    dssum_launch<float, true>(c, c->d_w32, c->d_p32, c->d_sc, c->d_partials, c->ax_grid);
+    dssum_launch<float, true>(c, c->d_w32, c->d_sc, c->d_partials, c->ax_grid);
     NB_LAUNCH_CHECK("dssum_kernel<f32,cg>");
     return NB_OK;
 }
@@ -268,7 +235,7 @@ nb_status launch_dssum32(nb_ctx *c, float *w) {
     shared_counts(c->m, cx, cy, cz);
     if ((int64_t)cx + cy + cz == 0) return NB_OK;
     LaunchTimer tm(c, NB_K_DSSUM);
-    dssum_launch<float, false>(c, w, nullptr, nullptr, nullptr, 0);
+    dssum_launch<float, false>(c, w, nullptr, nullptr, 0);
     NB_LAUNCH_CHECK("dssum_kernel<f32>");
     return NB_OK;
 }
