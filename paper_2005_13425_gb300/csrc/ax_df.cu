@@ -45,15 +45,10 @@ struct AxDfArgs {
     int64_t E;
 };
 
-// Four CTAs per SM fit the shared memory at n <= 10; the register bound
-// keeps them resident.
-template <int N>
-__host__ __device__ constexpr int ax_df_min_blocks() {
-    return N <= 10 ? 4 : 1;
-}
-
+// As many CTAs per SM as the shared memory holds (df_min_blocks); the
+// register bound keeps them resident.
 template <int N, int MODE, bool EO>
-__global__ void __launch_bounds__(ax_df_threads(N), ax_df_min_blocks<N>())
+__global__ void __launch_bounds__(ax_df_threads(N), df_min_blocks<N, ax_df_threads(N)>())
 ax_df_kernel(AxDfArgs a, const __grid_constant__ typename DfConsts<N, EO>::type D) {
     constexpr int N3 = N * N * N;
     extern __shared__ float2 sm[];

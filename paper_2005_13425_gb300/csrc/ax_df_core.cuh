@@ -51,6 +51,19 @@ __host__ __device__ constexpr int df_threads_lpt(int n, int lpt) {
     return ((3 * n * n + lpt - 1) / lpt + 31) / 32 * 32;
 }
 
+// CTAs of T threads per SM that the register bound of a kernel around the
+// element operator asks for: as many as the six n^3 pair arrays allow in
+// 228 KB of shared memory (1 KB reserved per CTA), but no more than leave R
+// registers per thread (a line at n <= 10 needs 48; the batched kernel's
+// tile bookkeeping needs more); 4 at n = 10, 2 at n = 11, 12 for R = 48.
+// Above n = 12 a line's registers cannot be bounded without spilling.
+template <int N, int T, int R = 48>
+__host__ __device__ constexpr int df_min_blocks() {
+    constexpr int by_smem = (228 * 1024) / (6 * N * N * N * 8 + 1024);
+    constexpr int by_regs = 65536 / (T * R);
+    return N > 12 ? 1 : (N > 10 ? by_smem : (by_smem < by_regs ? by_smem : by_regs));
+}
+
 // Line task -> (first point, stride) of the line and the direction.
 template <int N>
 __device__ __forceinline__ int line_of(int task, int &stride) {

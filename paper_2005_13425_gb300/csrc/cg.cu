@@ -56,6 +56,12 @@ static int red_grid(const nb_ctx *c) {
     return (int)(c->m.E < cap ? c->m.E : cap);
 }
 
+// The update kernel: six CTAs per SM (its register bound), one wave.
+static int update_grid(const nb_ctx *c) {
+    const int64_t cap = (int64_t)sms() * 6;
+    return (int)(c->m.E < cap ? c->m.E : cap);
+}
+
 // MODE 0: *out = <a,b>_c.
 // MODE 1 (unfused solver step): pap = <w,p>_c, alpha = rho/pap.
 // MODE 2 (solver start): r = f - w, p = 0, rho = <r,z>_c (z = minv r or r),
@@ -165,7 +171,7 @@ __device__ __forceinline__ void update_body(double *__restrict__ r, const double
 // rho = rr), beta = rho/rho_old, convergence decision on rr.  PRE selects
 // the Jacobi form at compile time so the plain kernel carries none of it.
 template <int N, bool PRE>
-__global__ void __launch_bounds__(kRedThreads)
+__global__ void __launch_bounds__(kRedThreads, 6)
 update_kernel(double *__restrict__ r, const double *__restrict__ w, Mesh m, double *partials,
               CgScalars *sc, double *hist, const double *__restrict__ minv) {
     if (sc->done) return;
@@ -238,10 +244,10 @@ static void dot_launch(nb_ctx *c, int mode, const double *a, const double *b, do
 template <int N>
 static void update_launch(nb_ctx *c) {
     if (c->d_minv)
-        update_kernel<N, true><<<red_grid(c), kRedThreads, 0, c->stream>>>(c->d_r, c->d_w, c->m, c->d_partials,
+        update_kernel<N, true><<<update_grid(c), kRedThreads, 0, c->stream>>>(c->d_r, c->d_w, c->m, c->d_partials,
                                                                           c->d_sc, c->d_hist, c->d_minv);
     else
-        update_kernel<N, false><<<red_grid(c), kRedThreads, 0, c->stream>>>(c->d_r, c->d_w, c->m,
+        update_kernel<N, false><<<update_grid(c), kRedThreads, 0, c->stream>>>(c->d_r, c->d_w, c->m,
                                                                            c->d_partials, c->d_sc, c->d_hist,
                                                                            nullptr);
 }

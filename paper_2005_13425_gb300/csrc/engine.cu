@@ -71,7 +71,7 @@ struct ProbDesc {
 // ---------------------------------------------------------------- kernels
 // CG head over a list of (slot, tile) work units.
 template <int N, int T>
-__global__ void __launch_bounds__(T, (T <= 320 ? 3 : 1))
+__global__ void __launch_bounds__(T, df_min_blocks<N, T, 64>())
 eng_ax_head(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles,
             const __grid_constant__ DfEo<N> D) {
     constexpr int N3 = N * N * N;
@@ -181,7 +181,7 @@ eng_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int
 // r -= alpha w with <r,r>_c per tile; the problem's last tile forms rho,
 // beta and the convergence decision.
 template <int N>
-__global__ void __launch_bounds__(kEngThreads)
+__global__ void __launch_bounds__(kEngThreads, 6)
 eng_update(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles) {
     constexpr int N3 = N * N * N;
     constexpr int K = (N3 + kEngThreads - 1) / kEngThreads;   // points per thread per element
@@ -458,7 +458,7 @@ eng_m_dssum(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const i
 // the inner convergence test; a finished inner solve hands the problem to
 // the outer step.
 template <int N>
-__global__ void __launch_bounds__(kEngThreads)
+__global__ void __launch_bounds__(kEngThreads, 6)
 eng_m_update(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles) {
     constexpr int N3 = N * N * N;
     constexpr int K = (N3 + kEngThreads - 1) / kEngThreads;   // points per thread per element
@@ -821,7 +821,7 @@ static nb_status group_iteration(nb_engine *g, const NGroup &G) {
     if (s != NB_OK) return s;
     eng_dssum<N><<<g->sms * 8, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ds, G.d_cnt + 1);
     NB_LAUNCH_CHECK("eng_dssum");
-    eng_update<N><<<g->sms * 4, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ax, G.d_cnt);
+    eng_update<N><<<g->sms * 6, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ax, G.d_cnt);
     NB_LAUNCH_CHECK("eng_update");
     return NB_OK;
 }
@@ -870,7 +870,7 @@ static nb_status mixed_inner_iteration(nb_engine *g, const NGroup &G) {
     NB_LAUNCH_CHECK("eng_m_head");
     eng_m_dssum<float, true, N><<<g->sms * 8, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ds, G.d_cnt + 1);
     NB_LAUNCH_CHECK("eng_m_dssum");
-    eng_m_update<N><<<g->sms * 4, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ax, G.d_cnt);
+    eng_m_update<N><<<g->sms * 6, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ax, G.d_cnt);
     NB_LAUNCH_CHECK("eng_m_update");
     return NB_OK;
 }

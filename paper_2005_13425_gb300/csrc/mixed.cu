@@ -94,7 +94,7 @@ inner_start_kernel(const float *__restrict__ r, float *__restrict__ p, float *__
 
 // r -= alpha w (FP32 vectors), rho = <r,r>_c in FP64, beta, convergence.
 template <int N>
-__global__ void __launch_bounds__(kT)
+__global__ void __launch_bounds__(kT, 6)
 inner_update_kernel(float *__restrict__ r, const float *__restrict__ w, Mesh m, double *partials,
                     CgScalars *sc) {
     constexpr int N3 = N * N * N;
@@ -161,6 +161,12 @@ static int grid_e(const nb_ctx *c) {
     return (int)(c->m.E < cap ? c->m.E : cap);
 }
 
+// The inner update: six CTAs per SM (its register bound), one wave.
+static int grid_update(const nb_ctx *c) {
+    const int64_t cap = (int64_t)sms32() * 6;
+    return (int)(c->m.E < cap ? c->m.E : cap);
+}
+
 static nb_status inner_start(nb_ctx *c) {
     LaunchTimer tm(c, NB_K_DOT);
 #define CALL(NN)                                                                                    \
@@ -175,7 +181,7 @@ static nb_status inner_start(nb_ctx *c) {
 static nb_status inner_update(nb_ctx *c) {
     LaunchTimer tm(c, NB_K_UPDATE);
 #define CALL(NN)                                                                                    \
-    inner_update_kernel<NN><<<grid_e(c), kT, 0, c->stream>>>(c->d_r32, c->d_w32, c->m, c->d_partials, \
+    inner_update_kernel<NN><<<grid_update(c), kT, 0, c->stream>>>(c->d_r32, c->d_w32, c->m, c->d_partials, \
                                                              c->d_sc)
     NB_DISPATCH_N32(c->m.n, CALL)
 #undef CALL
