@@ -21,6 +21,7 @@
 
 #include <mutex>
 
+#include "df.cuh"
 #include "internal.cuh"
 #include "reduce.cuh"
 
@@ -140,9 +141,10 @@ dot_kernel(const double *__restrict__ a, const double *__restrict__ b, double *_
 template <int N, bool PRE>
 __device__ __forceinline__ void update_body(double *__restrict__ r, const double *__restrict__ w, const Mesh &m,
                                             double alpha, const double *__restrict__ minv, double &acc,
-                                            double &accz) {
+                                            double &accz, int sh) {
     constexpr int N3 = N * N * N;
     constexpr int K = (N3 + kRedThreads - 1) / kRedThreads;   // points per thread per element
+    dfa::SqAcc32 sq;
     unsigned pf[K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
@@ -161,10 +163,18 @@ __device__ __forceinline__ void update_body(double *__restrict__ r, const double
             const double rn = fma(-alpha, __ldcs(w + base + q), r[base + q]);
             r[base + q] = rn;
             const int lg = __popc(pf[k] & sf);
-            acc = fma(scale_down_pow2(rn, lg), rn, acc);
-            if (PRE) accz = fma(scale_down_pow2(rn * minv[base + q], lg), rn, accz);
+            if (PRE) {
+                acc = fma(scale_down_pow2(rn, lg), rn, acc);
+                accz = fma(scale_down_pow2(rn * minv[base + q], lg), rn, accz);
+            } else {
+                // <r,r>_c on the FP32 pipes: r 2^sh split into a pair with
+                // integer operations, squares accumulated compensated
+                const float2 v = dfa::split_scaled<true>(rn, sh);
+                sq.add_sq(v.x, v.y, __uint_as_float((127u - (unsigned)lg) << 23));
+            }
         }
     }
+    if (!PRE) acc = sq.value() * __longlong_as_double((long long)(1023 - 2 * sh) << 52);
 }
 
 // r -= alpha w, rr = <r,r>_c, rho = <r,z>_c (z = minv r with Jacobi, else
@@ -177,7 +187,12 @@ update_kernel(double *__restrict__ r, const double *__restrict__ w, Mesh m, doub
     if (sc->done) return;
     const double alpha = sc->alpha;
     double acc = 0.0, accz = 0.0, rr, rho;
-    update_body<N, PRE>(r, w, m, alpha, minv, acc, accz);
+    // scale 2^sh with (r 2^sh)^2 of order one: from the previous <r,r>_c
+    // (the residual changes by modest factors per iteration; the FP32
+    // range leaves 2^+-60 of room either way)
+    const int erb = (int)((__double_as_longlong(sc->rr) >> 52) & 0x7ff);
+    const int sh = erb == 0 ? 0 : -((erb - 1023) >> 1);
+    update_body<N, PRE>(r, w, m, alpha, minv, acc, accz, sh);
     if (PRE) {
         double v[2] = {acc, accz}, tot[2];
         if (!last_block_reduce<2>(v, partials, gridDim.x, blockIdx.x, gridDim.x, gridDim.x, &sc->ticket, tot))

@@ -95,6 +95,26 @@ struct Acc32 {
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// Compensated FP32 accumulation of weighted squares cw (h + l)^2 of pairs
+// (cw a power of two): the product h^2 is exact (TwoProd), the cross term
+// 2hl rides with its error, l^2 (below 2^-46 relative) is dropped.  Each
+// term is accurate to about 2^-45 relative, the sum adds compensated; used
+// for <r,r>_c on the FP32 pipes, where the FP64 pipe is the bottleneck.
+struct SqAcc32 {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add_sq(float h, float l, float cw) {
+        const float hc = __fmul_rn(h, cw);                 // exact: cw = 2^-k
+        const float p = __fmul_rn(hc, h);
+        const float e = __fmaf_rn(hc, h, -p);              // exact rounding error of hc h
+        const float x = __fmaf_rn(__fmul_rn(2.f, hc), l, e);
+        float t, err;
+        two_sum(s, p, t, err);
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(err, x));
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // Split a double into a normalised pair: h = fl32(x), l = fl32(x - h).
 // x - h is exact in FP64, so h + l carries 48 bits of x.
 __device__ __forceinline__ float2 split(double x) {
@@ -111,7 +131,10 @@ __device__ __forceinline__ double join(float2 v) { return (double)v.x + (double)
 // (truncated), both with x's sign; |x*2^sh - (h + l)| < 2^-46 |x*2^sh|.
 // Values whose scaled magnitude falls below 2^-126 become (0, 0): callers
 // scale so that the data's maximum is in [1, 2), which makes that an
-// absolute error below 2^-126 of the maximum.
+// absolute error below 2^-126 of the maximum.  With SAT, magnitudes at or
+// above 2^128 after scaling become (+-inf, 0) (callers whose scale is an
+// estimate); without it the caller guarantees they do not occur.
+template <bool SAT = false>
 __device__ __forceinline__ float2 split_scaled(double x, int sh) {
     const long long b = __double_as_longlong(x);
     const unsigned hi32 = (unsigned)((unsigned long long)b >> 32), lo32 = (unsigned)b;
@@ -119,6 +142,7 @@ __device__ __forceinline__ float2 split_scaled(double x, int sh) {
     const int e = (int)((hi32 >> 20) & 0x7ffu);
     const int ef = e - 1023 + sh + 127;                  // float exponent field of h
     if (e == 0 || ef < 1) return make_float2(0.f, 0.f);
+    if (SAT && ef > 254) return make_float2(__uint_as_float(sign | 0x7f800000u), 0.f);
     const unsigned mh = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
     const float h = __uint_as_float(sign | ((unsigned)ef << 23) | mh);
     const int el = ef - 46;                              // exponent field of the unit 2^(e-1069+sh)

@@ -202,7 +202,11 @@ eng_update(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const in
         const double alpha = P.sc.alpha;
         const int64_t e0 = (int64_t)tile.y * P.te;
         const int64_t e1 = e0 + P.te < m.E ? e0 + P.te : m.E;
-        double acc = 0.0;
+        // <r,r>_c on the FP32 pipes (see update_body in cg.cu): r 2^sh split
+        // into pairs, squares accumulated compensated
+        const int erb = (int)((__double_as_longlong(P.sc.rr) >> 52) & 0x7ff);
+        const int sh = erb == 0 ? 0 : -((erb - 1023) >> 1);
+        dfa::SqAcc32 sq;
         for (int64_t e = e0; e < e1; e++) {
             int ex, ey, ez;
             element_coords(e, m, ex, ey, ez);
@@ -215,9 +219,11 @@ eng_update(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const in
                 if (K * kEngThreads != N3 && q >= N3) break;
                 const double rn = fma(-alpha, __ldcs(w + q), r[q]);
                 r[q] = rn;
-                acc = fma(scale_down_pow2(rn, __popc(pf[k] & sf)), rn, acc);
+                const float2 v = dfa::split_scaled<true>(rn, sh);
+                sq.add_sq(v.x, v.y, __uint_as_float((127u - (unsigned)__popc(pf[k] & sf)) << 23));
             }
         }
+        const double acc = sq.value() * __longlong_as_double((long long)(1023 - 2 * sh) << 52);
         const double b = block_sum(acc, red);
         if (threadIdx.x == 0) {
             P.partials[tile.y] = b;
