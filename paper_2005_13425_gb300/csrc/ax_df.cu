@@ -36,8 +36,9 @@ struct AxDfArgs {
     double *p;            // MODE 1: search direction, updated in place
     double *x;            // MODE 1: iterate, receives the owed x += x_alpha p
     const double *minv;   // MODE 1: Jacobi inverse diagonal or null
-    const CgScalars *sc;  // MODE 1
+    CgScalars *sc;        // MODE 1
     double *partials;     // MODE 1 fused: one <w,p> partial per CTA
+    int finalize;         // MODE 1 fused: the last CTA reduces <w,p>_c and forms alpha
     int fuse;             // MODE 1: zero box-face points, local products w p
     Mesh m;
     const float2 *g;      // gxyz pairs [E][6][n^3], scaled by 2^-(gexp-1023)
@@ -77,8 +78,15 @@ ax_df_kernel(AxDfArgs a, const __grid_constant__ typename DfConsts<N, EO>::type 
         df_element<N, MODE, EO>(io, beta, xa, a.fuse != 0, a.gexp, a.m, ex, ey, ez, D, sm, &s_emax, dot);
     }
     if (MODE == 1 && a.fuse) {
-        const double b = block_sum(dot, red);
-        if (threadIdx.x == 0) a.partials[blockIdx.x] = b;
+        if (a.finalize) {
+            double v[1] = {dot}, tot[1];
+            if (last_block_reduce<1>(v, a.partials, 0, blockIdx.x, gridDim.x, gridDim.x, &a.sc->ticket, tot) &&
+                threadIdx.x == 0)
+                finalize_alpha(a.sc, tot[0]);
+        } else {
+            const double b = block_sum(dot, red);
+            if (threadIdx.x == 0) a.partials[blockIdx.x] = b;
+        }
     }
 }
 
@@ -167,6 +175,7 @@ static nb_status launch_df_nv(nb_ctx *c, const double *u, double *w, int mode) {
         args.sc = c->d_sc;
         args.partials = c->d_partials;
         args.fuse = c->fused_cg ? 1 : 0;
+        args.finalize = c->two_kernel ? 1 : 0;
     }
     args.m = c->m;
     auto kern = mode == 0 ? ax_df_kernel<N, 0, EO> : ax_df_kernel<N, 1, EO>;

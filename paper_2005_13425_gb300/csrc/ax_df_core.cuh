@@ -186,12 +186,6 @@ __device__ __forceinline__ void df_point_masks(unsigned *pf) {
     }
 }
 
-// Faces of element (ex,ey,ez) on the box boundary, in point_faces' bit order.
-__device__ __forceinline__ unsigned box_faces(int ex, int ey, int ez, const Mesh &m) {
-    return (unsigned)(ex == 0) | ((unsigned)(ex == m.ex - 1) << 1) | ((unsigned)(ey == 0) << 2) |
-           ((unsigned)(ey == m.ey - 1) << 3) | ((unsigned)(ez == 0) << 4) | ((unsigned)(ez == m.ez - 1) << 5);
-}
-
 // One element of ax_e in double-float arithmetic, executed by the whole CTA
 // (every thread must call it; it contains barriers).  sm holds 6 n^3 pairs,
 // s_emax is a shared int that must be 0 on entry (left 0 on exit).

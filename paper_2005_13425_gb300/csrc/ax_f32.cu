@@ -19,8 +19,9 @@ struct AxF32Args {
     const float *r;       // MODE 1: inner residual
     float *p;             // MODE 1: inner search direction
     float *x;             // MODE 1: inner solution, receives the owed update
-    const CgScalars *sc;  // MODE 1
-    double *partials;     // MODE 1: one <w,p> partial per CTA (element interiors)
+    CgScalars *sc;        // MODE 1
+    double *partials;     // MODE 1: one <w,p> partial per CTA (local products)
+    int finalize;         // MODE 1: the last CTA reduces <w,p>_c and forms alpha
     Mesh m;
     const float *g;       // gxyz [E][6][n^3], FP32
     int64_t E;
@@ -56,8 +57,15 @@ ax_f32_kernel(AxF32Args a, const __grid_constant__ F32Mat<N> D) {
         f32_element<N, MODE, T>(io, beta, xa, ex, ey, ez, a.m, D, smf, dot);
     }
     if (MODE == 1) {
-        const double b = block_sum(dot.value(), red);
-        if (threadIdx.x == 0) a.partials[blockIdx.x] = b;
+        if (a.finalize) {
+            double v[1] = {dot.value()}, tot[1];
+            if (last_block_reduce<1>(v, a.partials, 0, blockIdx.x, gridDim.x, gridDim.x, &a.sc->ticket, tot) &&
+                threadIdx.x == 0)
+                finalize_alpha(a.sc, tot[0]);
+        } else {
+            const double b = block_sum(dot.value(), red);
+            if (threadIdx.x == 0) a.partials[blockIdx.x] = b;
+        }
     }
 }
 
@@ -91,14 +99,17 @@ ax_f32_staged_kernel(AxF32Args a, CgScalars *err, const __grid_constant__ F32Mat
     __syncthreads();
     const bool with_x = MODE == 1 && xa != 0.f;
     const unsigned bytes = 4u * (MODE == 1 ? (with_x ? 9 : 8) : 7) * N3;
+    // the geometric factors and x are read once per iteration: evict them
+    // first, so p and w stay in L2 for the dssum and update kernels
+    const uint64_t stream_pol = t == 0 ? l2_evict_first_policy() : 0ull;
     auto issue = [&](int64_t e, int s) {   // thread 0
         float *st = smf + s * STAGE;
         mbar_expect_tx(&bars[s], bytes);
-        bulk_g2s(st, a.g + e * 6 * N3, 4u * 6 * N3, &bars[s]);
+        bulk_g2s_hint(st, a.g + e * 6 * N3, 4u * 6 * N3, &bars[s], stream_pol);
         if (MODE == 1) {
             bulk_g2s(st + 6 * N3, a.r + e * N3, 4u * N3, &bars[s]);
             bulk_g2s(st + 7 * N3, a.p + e * N3, 4u * N3, &bars[s]);
-            if (with_x) bulk_g2s(st + 8 * N3, a.x + e * N3, 4u * N3, &bars[s]);
+            if (with_x) bulk_g2s_hint(st + 8 * N3, a.x + e * N3, 4u * N3, &bars[s], stream_pol);
         } else {
             bulk_g2s(st + 6 * N3, a.u + e * N3, 4u * N3, &bars[s]);
         }
@@ -138,8 +149,15 @@ ax_f32_staged_kernel(AxF32Args a, CgScalars *err, const __grid_constant__ F32Mat
         __syncthreads();
     }
     if (MODE == 1) {
-        const double b = block_sum(dot.value(), red);
-        if (threadIdx.x == 0) a.partials[blockIdx.x] = b;
+        if (a.finalize) {
+            double v[1] = {dot.value()}, tot[1];
+            if (last_block_reduce<1>(v, a.partials, 0, blockIdx.x, gridDim.x, gridDim.x, &a.sc->ticket, tot) &&
+                threadIdx.x == 0)
+                finalize_alpha(a.sc, tot[0]);
+        } else {
+            const double b = block_sum(dot.value(), red);
+            if (threadIdx.x == 0) a.partials[blockIdx.x] = b;
+        }
     }
 }
 
@@ -167,6 +185,7 @@ static nb_status launch_f32_n(nb_ctx *c, const float *u, float *w, int mode) {
         args.w = c->d_w32;
         args.sc = c->d_sc;
         args.partials = c->d_partials;
+        args.finalize = c->two_kernel ? 1 : 0;
     }
     if constexpr (f32_staged_ok<N>()) {
         if (!c->f32_plain) {

@@ -152,11 +152,11 @@ __device__ __forceinline__ void f32_element(const F32ElemIO &io, float beta, flo
         }
     }
     __syncthreads();
+    const unsigned bf = MODE == 1 ? box_faces(ex, ey, ez, m) : 0u;
     for (int q = t; q < N3; q += T) {
         float wv = U[q] + P1[q] + P2[q];
         if (MODE == 1) {
-            const int i = q % N, j = (q / N) % N, k = q / N2;
-            if (on_box_face(i, j, k, ex, ey, ez, m))
+            if (point_faces<N>(q) & bf)
                 wv = 0.f;
             else
                 dot.add_prod(wv, io.p[q]);
@@ -272,11 +272,11 @@ __device__ __forceinline__ void f32_element_staged(float *st, float *W, const F3
         }
     }
     __syncthreads();
+    const unsigned bf = MODE == 1 ? box_faces(ex, ey, ez, m) : 0u;
     for (int q = t; q < N3; q += T) {
         float wv = P0[q] + P1[q] + P2[q];
         if (MODE == 1) {
-            const int i = q % N, j = (q / N) % N, k = q / N2;
-            if (on_box_face(i, j, k, ex, ey, ez, m))
+            if (point_faces<N>(q) & bf)
                 wv = 0.f;
             else
                 dot.add_prod(wv, U[q]);

@@ -33,6 +33,7 @@ bool df_supported(int n);
 nb_status launch_dssum_sc(nb_ctx *c, double *w, const CgScalars *sc);
 nb_status launch_dssum_cg(nb_ctx *c);
 nb_status launch_mask_sc(nb_ctx *c, double *w, const CgScalars *sc);
+nb_status launch_assemble_update(nb_ctx *c);
 int dssum_grid(const nb_ctx *c);
 
 constexpr int kRedThreads = 256;
@@ -324,6 +325,10 @@ static nb_status ensure_hist(nb_ctx *c, int maxit) {
         NB_CUDA(cudaStreamSynchronize(c->stream));
         cudaFree(c->d_hist);
         c->d_hist = nullptr;
+        if (c->cg_graph) {   // the captured iteration writes the old history buffer
+            cudaGraphExecDestroy(c->cg_graph);
+            c->cg_graph = nullptr;
+        }
     }
     int cap = maxit + 1 < 1024 ? 1024 : maxit + 1;
     cudaError_t e = dev_alloc((void **)&c->d_hist, sizeof(double) * cap);
@@ -350,6 +355,7 @@ nb_status dot_c(nb_ctx *c, const double *a, const double *b, double *out_host) {
 static nb_status enqueue_iteration(nb_ctx *c) {
     nb_status s;
     if ((s = launch_ax_cg(c)) != NB_OK) return s;
+    if (c->two_kernel) return launch_assemble_update(c);
     if (c->fused_cg) {
         if ((s = launch_dssum_cg(c)) != NB_OK) return s;
     } else {
@@ -361,7 +367,7 @@ static nb_status enqueue_iteration(nb_ctx *c) {
 }
 
 static nb_status build_graph(nb_ctx *c, int chunk) {
-    if (c->cg_graph && c->cg_graph_chunk == chunk) return NB_OK;
+    if (c->cg_graph && c->cg_graph_chunk == chunk && c->cg_graph_two == c->two_kernel) return NB_OK;
     if (c->cg_graph) {
         cudaGraphExecDestroy(c->cg_graph);
         c->cg_graph = nullptr;
@@ -380,6 +386,7 @@ static nb_status build_graph(nb_ctx *c, int chunk) {
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     c->cg_graph_chunk = chunk;
+    c->cg_graph_two = c->two_kernel;
     return NB_OK;
 }
 
@@ -389,6 +396,7 @@ nb_status cg_solve_fp64(nb_ctx *c, const double *f, double *x, double tol, int m
     if ((s = ensure_cg_workspace(c)) != NB_OK) return s;
     if ((s = ensure_hist(c, maxit)) != NB_OK) return s;
     c->fused_cg = c->d_mask == nullptr;
+    c->two_kernel = c->fused_cg && !c->d_minv && use_df(c);
     const size_t bytes = sizeof(double) * c->m.npts;
     CgScalars init{};
     init.tol = tol;

@@ -98,11 +98,13 @@ struct nb_ctx {
     int last_iters = 0;
     int ax_grid = 0;                    // partial slots written by the fused ax_e
     bool fused_cg = false;              // box mask: fused CG iteration
+    bool two_kernel = false;            // fused and no preconditioner: head + assemble_update
     // mixed precision workspace
     float *d_r32 = nullptr, *d_p32 = nullptr, *d_w32 = nullptr, *d_z32 = nullptr;
     // CUDA graphs of chunks of FP64 and FP32 (inner) CG iterations
     cudaGraphExec_t cg_graph = nullptr;
     int cg_graph_chunk = 0;
+    bool cg_graph_two = false;          // the iteration form captured in cg_graph
     cudaGraphExec_t cg_graph32 = nullptr;
     int cg_graph32_chunk = 0;
     // mixed-precision parameters and statistics

@@ -29,6 +29,7 @@ nb_status launch_dssum_sc(nb_ctx *c, double *w, const CgScalars *sc);
 nb_status launch_mask_sc(nb_ctx *c, double *w, const CgScalars *sc);
 nb_status launch_ax(nb_ctx *c, const double *u, double *w);
 nb_status dot_start(nb_ctx *c, const double *f);   // cg.cu: r = f - w, rho, fnorm2
+nb_status launch_assemble_update32(nb_ctx *c);     // assemble.cu
 
 constexpr int kT = 256;
 
@@ -189,11 +190,12 @@ static nb_status inner_update(nb_ctx *c) {
     return NB_OK;
 }
 
+// One inner iteration: the FP32 head (whose last CTA forms alpha), then
+// dssum fused with the residual update (assemble.cu).
 static nb_status inner_iteration(nb_ctx *c) {
     nb_status s;
     if ((s = launch_ax_f32(c, nullptr, nullptr, 1)) != NB_OK) return s;
-    if ((s = launch_dssum_cg32(c)) != NB_OK) return s;
-    return inner_update(c);
+    return launch_assemble_update32(c);
 }
 
 static nb_status build_graph32(nb_ctx *c, int chunk) {
@@ -240,6 +242,7 @@ nb_status cg_solve_mixed(nb_ctx *c, const double *f, double *x, double tol, int 
     nb_status s;
     if ((s = ensure_cg_workspace(c)) != NB_OK) return s;
     if (c->d_mask) return fail(NB_ERR_STATE, "the mixed-precision solve supports the box mask only");
+    c->two_kernel = true;   // inner iterations: head + assemble_update
     const double inner_tol = c->mixed_inner_tol > 0.0 ? c->mixed_inner_tol : 1e-4;
     const int max_outer = c->mixed_max_outer > 0 ? c->mixed_max_outer : 50;
     const size_t bytes = sizeof(double) * c->m.npts;

@@ -62,6 +62,20 @@ __device__ bool last_block_reduce(const double (&v)[NV], double *partials, int s
     return true;
 }
 
+// The CG step after <w,p>_c is known: alpha = rho/<w,p>_c, or a breakdown
+// flag when <w,p>_c <= 0 or is not finite (the owed x update is dropped).
+__device__ __forceinline__ void finalize_alpha(CgScalars *sc, double pap) {
+    sc->pap = pap;
+    if (!(pap > 0.0) || !isfinite(pap)) {
+        sc->status = (int)NB_ERR_BREAKDOWN;
+        sc->done = 1;
+        sc->x_alpha = 0.0;
+    } else {
+        sc->alpha = sc->rho / pap;
+        sc->x_alpha = sc->alpha;
+    }
+}
+
 // Copies of local point (i,j,k) of element (ex,ey,ez) -> 1/multiplicity.
 __device__ __forceinline__ double inv_mult(int i, int j, int k, int ex, int ey, int ez, const Mesh &m) {
     const int mu = mult_1d(i, ex, m.ex, m.n) * mult_1d(j, ey, m.ey, m.n) * mult_1d(k, ez, m.ez, m.n);
@@ -104,6 +118,12 @@ __device__ __forceinline__ unsigned point_faces(int q) {
 __device__ __forceinline__ unsigned shared_faces(int ex, int ey, int ez, const Mesh &m) {
     return (unsigned)(ex > 0) | ((unsigned)(ex < m.ex - 1) << 1) | ((unsigned)(ey > 0) << 2) |
            ((unsigned)(ey < m.ey - 1) << 3) | ((unsigned)(ez > 0) << 4) | ((unsigned)(ez < m.ez - 1) << 5);
+}
+
+// Faces of element (ex,ey,ez) on the box boundary, in point_faces' bit order.
+__device__ __forceinline__ unsigned box_faces(int ex, int ey, int ez, const Mesh &m) {
+    return (unsigned)(ex == 0) | ((unsigned)(ex == m.ex - 1) << 1) | ((unsigned)(ey == 0) << 2) |
+           ((unsigned)(ey == m.ey - 1) << 3) | ((unsigned)(ez == 0) << 4) | ((unsigned)(ez == m.ez - 1) << 5);
 }
 
 // Element id -> (ex, ey, ez) with 32-bit arithmetic.
