@@ -220,15 +220,6 @@ nb_status launch_dssum_cg(nb_ctx *c) {
     return NB_OK;
 }
 
-// The same fused step for the FP32 inner solve of the mixed-precision path:
-// node sums in FP32 (ascending element order); <w,p>_c (from the head) in FP64.
-nb_status launch_dssum_cg32(nb_ctx *c) {
-    LaunchTimer tm(c, NB_K_DSSUM);
-    dssum_launch<float, true>(c, c->d_w32, c->d_sc, c->d_partials, c->ax_grid);
-    NB_LAUNCH_CHECK("dssum_kernel<f32,cg>");
-    return NB_OK;
-}
-
 // Plain FP32 dssum (tests of the inner operator).
 nb_status launch_dssum32(nb_ctx *c, float *w) {
     int cx, cy, cz;

@@ -2,8 +2,8 @@
 // known at compile time and the mesh-dependent divisors replaced by exact
 // multiply-high reciprocals (Granlund and Montgomery, 1994: for d >= 2,
 // m = ceil(2^64 / d) gives floor(q / d) = floor(q m / 2^64) for every
-// 32-bit q, because q (m d - 2^64) < 2^64).  Same node order and copy
-// order as gs_nodes.cuh, so the sums are bit-identical.
+// 32-bit q, because q (m d - 2^64) < 2^64).  Each node's copies are listed
+// in ascending element order, the order in which dssum adds them.
 #pragma once
 
 #include "gs_nodes.cuh"
@@ -24,110 +24,6 @@ struct FastDiv {
         return d <= 1 ? q : (unsigned)__umul64hi((unsigned long long)q, m);
     }
 };
-
-// Everything the node decode needs about one box mesh.
-struct DsDecode {
-    int cx, cy, cz;                 // shared nodes on x-planes, y-planes (off x), z-planes (off x, y)
-    int ex, ey, ez;                 // elements per direction
-    int NX, NY, NZ, NXp, NYp;       // global nodes per direction; non-plane counts in x and y
-    FastDiv fNY, fNZ, fNXp, fNYp;
-};
-
-inline DsDecode make_ds_decode(const Mesh &m) {
-    DsDecode d;
-    shared_counts(m, d.cx, d.cy, d.cz);
-    d.ex = m.ex; d.ey = m.ey; d.ez = m.ez;
-    d.NX = (int)m.NX; d.NY = (int)m.NY; d.NZ = (int)m.NZ;
-    d.NXp = (int)(m.NX - (m.ex - 1));
-    d.NYp = (int)(m.NY - (m.ey - 1));
-    d.fNY = FastDiv::make((unsigned)d.NY);
-    d.fNZ = FastDiv::make((unsigned)d.NZ);
-    d.fNXp = FastDiv::make((unsigned)d.NXp);
-    d.fNYp = FastDiv::make((unsigned)d.NYp);
-    return d;
-}
-
-// Non-plane coordinate q (of NG - (ne - 1)) -> global coordinate.
-template <int N>
-__device__ __forceinline__ int nonplane_coord_n(int q, int ne, int NG) {
-    if (q == 0) return 0;
-    if (q == ne * (N - 2) + 1) return NG - 1;
-    if constexpr (N > 2) {
-        const int qq = q - 1;
-        return (qq / (N - 2)) * (N - 1) + 1 + qq % (N - 2);
-    }
-    return 0;
-}
-
-template <int N>
-__device__ __forceinline__ void shared_node_n(int q, const DsDecode &d, int &gx, int &gy, int &gz) {
-    constexpr int N1 = N - 1;
-    if (q < d.cx) {
-        unsigned r = (unsigned)q, t = d.fNY.div(r);
-        gy = (int)(r - t * (unsigned)d.NY);
-        r = t;
-        t = d.fNZ.div(r);
-        gz = (int)(r - t * (unsigned)d.NZ);
-        gx = (int)(t + 1) * N1;
-    } else if (q < d.cx + d.cy) {
-        unsigned r = (unsigned)(q - d.cx), t = d.fNXp.div(r);
-        gx = nonplane_coord_n<N>((int)(r - t * (unsigned)d.NXp), d.ex, d.NX);
-        r = t;
-        t = d.fNZ.div(r);
-        gz = (int)(r - t * (unsigned)d.NZ);
-        gy = (int)(t + 1) * N1;
-    } else {
-        unsigned r = (unsigned)(q - d.cx - d.cy), t = d.fNXp.div(r);
-        gx = nonplane_coord_n<N>((int)(r - t * (unsigned)d.NXp), d.ex, d.NX);
-        r = t;
-        t = d.fNYp.div(r);
-        gy = nonplane_coord_n<N>((int)(r - t * (unsigned)d.NYp), d.ey, d.NY);
-        gz = (int)(t + 1) * N1;
-    }
-}
-
-// Copies of global coordinate g along one direction (ascending element).
-template <int N>
-__device__ __forceinline__ int copies_1d_n(int g, int ne, int *el, int *li) {
-    constexpr int N1 = N - 1;
-    const int a = g / N1;
-    const int rem = g - a * N1;
-    if (rem == 0 && a > 0 && a < ne) {
-        el[0] = a - 1; li[0] = N1;
-        el[1] = a;     li[1] = 0;
-        return 2;
-    }
-    const int ee = a < ne ? a : ne - 1;
-    el[0] = ee;
-    li[0] = g - ee * N1;
-    return 1;
-}
-
-// Local indices of the copies of node (gx, gy, gz), ascending element order.
-template <int N>
-__device__ __forceinline__ int node_copies_n(int gx, int gy, int gz, const DsDecode &d, int64_t *idx) {
-    constexpr int64_t N3 = (int64_t)N * N * N;
-    int elx[2], lix[2], ely[2], liy[2], elz[2], liz[2];
-    const int nx = copies_1d_n<N>(gx, d.ex, elx, lix);
-    const int ny = copies_1d_n<N>(gy, d.ey, ely, liy);
-    const int nz = copies_1d_n<N>(gz, d.ez, elz, liz);
-    int c = 0;
-#pragma unroll
-    for (int a = 0; a < 2; a++) {
-        if (a >= nz) break;
-#pragma unroll
-        for (int b = 0; b < 2; b++) {
-            if (b >= ny) break;
-#pragma unroll
-            for (int x = 0; x < 2; x++) {
-                if (x >= nx) break;
-                const int64_t e = elx[x] + (int64_t)d.ex * (ely[b] + (int64_t)d.ey * elz[a]);
-                idx[c++] = e * N3 + lix[x] + N * (liy[b] + N * liz[a]);
-            }
-        }
-    }
-    return c;
-}
 
 }  // namespace nekgb
 

@@ -24,7 +24,6 @@
 namespace nekgb {
 
 nb_status launch_ax_f32(nb_ctx *c, const float *u, float *w, int mode);
-nb_status launch_dssum_cg32(nb_ctx *c);
 nb_status launch_dssum_sc(nb_ctx *c, double *w, const CgScalars *sc);
 nb_status launch_mask_sc(nb_ctx *c, double *w, const CgScalars *sc);
 nb_status launch_ax(nb_ctx *c, const double *u, double *w);
@@ -93,50 +92,6 @@ inner_start_kernel(const float *__restrict__ r, float *__restrict__ p, float *__
     sc->done = (tot[0] == 0.0 || sc->maxit == 0) ? 1 : 0;
 }
 
-// r -= alpha w (FP32 vectors), rho = <r,r>_c in FP64, beta, convergence.
-template <int N>
-__global__ void __launch_bounds__(kT, 6)
-inner_update_kernel(float *__restrict__ r, const float *__restrict__ w, Mesh m, double *partials,
-                    CgScalars *sc) {
-    constexpr int N3 = N * N * N;
-    constexpr int K = (N3 + kT - 1) / kT;   // points per thread per element
-    if (sc->done) return;
-    const float alpha = (float)sc->alpha;
-    dfa::Acc32 acc;   // exact products, compensated sums (FP64-class <r,r>_c)
-    unsigned pf[K];
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-        const int q = threadIdx.x + k * kT;
-        pf[k] = q < N3 ? point_faces<N>(q) : 0u;
-    }
-    for (int64_t e = blockIdx.x; e < m.E; e += gridDim.x) {
-        int ex, ey, ez;
-        element_coords(e, m, ex, ey, ez);
-        const unsigned sf = shared_faces(ex, ey, ez, m);
-        const int64_t base = e * N3;
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            const int q = threadIdx.x + k * kT;
-            if (K * kT != N3 && q >= N3) break;
-            const float rn = fmaf(-alpha, __ldcs(w + base + q), r[base + q]);
-            r[base + q] = rn;
-            const float cw = __uint_as_float((127u - __popc(pf[k] & sf)) << 23);  // 2^-lg
-            acc.add_prod(rn * cw, rn);
-        }
-    }
-    double v[1] = {acc.value()}, tot[1];
-    if (!last_block_reduce<1>(v, partials, 0, blockIdx.x, gridDim.x, gridDim.x, &sc->ticket, tot)) return;
-    if (threadIdx.x != 0) return;
-    const double rho = tot[0];
-    sc->rho_old = sc->rho;
-    sc->rho = rho;
-    sc->beta = rho / sc->rho_old;
-    const int it = sc->it + 1;
-    sc->it = it;
-    const bool conv = sqrt(rho) / sqrt(sc->fnorm2) <= sc->tol;
-    if (rho == 0.0 || conv || it >= sc->maxit) sc->done = 1;
-}
-
 __global__ void inner_final_kernel(float *__restrict__ x, const float *__restrict__ p, int64_t n,
                                    const CgScalars *__restrict__ sc) {
     const float xa = (float)sc->x_alpha;
@@ -162,12 +117,6 @@ static int grid_e(const nb_ctx *c) {
     return (int)(c->m.E < cap ? c->m.E : cap);
 }
 
-// The inner update: six CTAs per SM (its register bound), one wave.
-static int grid_update(const nb_ctx *c) {
-    const int64_t cap = (int64_t)sms32() * 6;
-    return (int)(c->m.E < cap ? c->m.E : cap);
-}
-
 static nb_status inner_start(nb_ctx *c) {
     LaunchTimer tm(c, NB_K_DOT);
 #define CALL(NN)                                                                                    \
@@ -176,17 +125,6 @@ static nb_status inner_start(nb_ctx *c) {
     NB_DISPATCH_N32(c->m.n, CALL)
 #undef CALL
     NB_LAUNCH_CHECK("inner_start_kernel");
-    return NB_OK;
-}
-
-static nb_status inner_update(nb_ctx *c) {
-    LaunchTimer tm(c, NB_K_UPDATE);
-#define CALL(NN)                                                                                    \
-    inner_update_kernel<NN><<<grid_update(c), kT, 0, c->stream>>>(c->d_r32, c->d_w32, c->m, c->d_partials, \
-                                                             c->d_sc)
-    NB_DISPATCH_N32(c->m.n, CALL)
-#undef CALL
-    NB_LAUNCH_CHECK("inner_update_kernel");
     return NB_OK;
 }
 

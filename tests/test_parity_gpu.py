@@ -267,6 +267,27 @@ def test_cg_fixed_100_iterations_config1(nek, oracle):
     assert abs(rr - rr_ref) <= 1e-8 * max(rr_ref, 1e-300) + 1e-14
 
 
+@pytest.mark.parametrize("dims,n", [((8, 6, 5), 2), ((4, 3, 2), 3), ((1, 1, 3), 7), ((2, 2, 2), 12),
+                                    ((2, 1, 1), 16), ((5, 4, 3), 5)])
+def test_cg_fixed_iterations_across_n(nek, oracle, dims, n):
+    """30 fixed iterations of the two-kernel iteration (head + fused
+    assemble/update) against the oracle's CG over the polynomial orders and
+    thin meshes (a single element along some directions leaves the edge and
+    vertex node ranges empty).  Every mesh has well over 30 unknowns, so the
+    iteration never runs into round-off after exact convergence."""
+    P, f = cg_inputs(oracle, dims, n, seed_mesh=n, seed_f=n + 1)
+    x_ref, it_ref, rr_ref, hist_ref, st = oracle.cg(*dims, n, P["D"], P["gxyz"], P["mask"], f,
+                                                    tol=0.0, maxit=30)
+    with Ctx(nek, dims, n, P["D"], P["gxyz"]) as ctx:
+        x = torch.zeros(P["E"], n ** 3, dtype=torch.float64, device="cuda")
+        st, it, rr = nek.nb_cg_solve(ctx, dev(f), x, tol=0.0, maxit=30)
+        xg = host(x)
+        hist = nek.nb_cg_history(ctx)
+    assert it == it_ref
+    assert np.abs(hist - hist_ref).max() / hist_ref.max() <= 1e-8
+    assert rel_err(xg, x_ref) <= 1e-8
+
+
 def test_cg_tolerance_and_determinism(nek, oracle):
     dims, n = (3, 2, 2), 6
     P, f = cg_inputs(oracle, dims, n, seed_mesh=3, seed_f=4)
