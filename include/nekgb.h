@@ -331,9 +331,10 @@ nb_status nb_engine_retire(nb_engine *eng, int id, double *x_dev);
 /* Arena bytes in use, arena capacity and active requests. */
 nb_status nb_engine_stats(const nb_engine *eng, size_t *used, size_t *capacity, int *active);
 
-/* The autotuner's choice for n: line tasks per thread and elements per
- * tile of the CG head kernel (0 if n has not been used yet). */
-nb_status nb_engine_tuning(const nb_engine *eng, int n, int *lines_per_thread,
+/* The autotuner's choice for (n, precision): line tasks per thread of the
+ * CG head (1 for NB_MIXED, whose FP32 head has one layout) and elements per
+ * tile (0 if that (n, precision) has not been used yet). */
+nb_status nb_engine_tuning(const nb_engine *eng, int n, nb_precision prec, int *lines_per_thread,
                            int *elems_per_tile);
 
 /* --------------------------------------------------------------------- */

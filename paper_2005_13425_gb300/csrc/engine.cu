@@ -15,9 +15,10 @@
 //   performs its scalar step.  A problem's arithmetic therefore depends only
 //   on the problem, never on what else is in the batch: results are
 //   bit-identical alone and in any mix.
-// * Autotuning: for each n the first use times the CG head kernel with one
-//   or two line tasks per thread and 4, 8 or 16 elements per tile on a
-//   synthetic problem, and caches the choice (NEKGB_TUNE_CACHE file).
+// * Autotuning: for each (n, precision) the first use times the CG
+//   iteration with one or two line tasks per thread (FP64 heads) and 4, 8
+//   or 16 elements per tile on a synthetic problem, and caches the choice
+//   (NEKGB_TUNE_CACHE file).
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -910,8 +911,9 @@ nb_status engine_step_internal(nb_engine *g, int iters);
 
 // Time the CG iteration of a synthetic 8x8x8-element problem for each
 // candidate (lines per thread, elements per tile) and keep the fastest.
-static nb_status autotune(nb_engine *g, int n) {
-    NGroup &G = g->groups[n];
+static nb_status autotune(nb_engine *g, int n, int prec) {
+    const bool mixed = prec == NB_MIXED;
+    NGroup &G = mixed ? g->mgroups[n] : g->groups[n];
     if (G.lpt) return NB_OK;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     int dev = 0;
@@ -919,7 +921,8 @@ static nb_status autotune(nb_engine *g, int n) {
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, dev);
     char key[512];
-    snprintf(key, sizeof key, "n%d_fp64_sm%d_%.200s", n, prop.multiProcessorCount, prop.name);
+    snprintf(key, sizeof key, "n%d_%s_sm%d_%.200s", n, mixed ? "mixed" : "fp64", prop.multiProcessorCount,
+             prop.name);
     for (char *c = key; *c; c++)
         if (*c == ' ') *c = '_';
     int lpt = 0, te = 0;
@@ -931,7 +934,7 @@ static nb_status autotune(nb_engine *g, int n) {
     const int lpts[2] = {1, 2};
     const int tes[3] = {4, 8, 16};
     float best = 1e30f;
-    int bl = n >= 13 ? 2 : 1, bt = 8;
+    int bl = !mixed && n >= 13 ? 2 : 1, bt = 8;
     const nb_box box = {8, 8, 8};
     const Mesh m = make_mesh(box, n);
     double *f = nullptr;
@@ -944,8 +947,9 @@ static nb_status autotune(nb_engine *g, int n) {
     cudaEventCreate(&b);
     nb_status st = NB_OK;
     for (int li = 0; li < 2 && st == NB_OK; li++) {
-        if (n >= 13 && lpts[li] == 1) continue;
-        if (head_spills(n, lpts[li])) continue;   // a variant that spills registers is never the fastest
+        if (mixed && li == 1) break;              // the FP32 head has one thread layout (lines per thread 1)
+        if (!mixed && n >= 13 && lpts[li] == 1) continue;
+        if (!mixed && head_spills(n, lpts[li])) continue;   // a variant that spills is never the fastest
         for (int ti = 0; ti < 3 && st == NB_OK; ti++) {
             G.lpt = lpts[li];
             if (g->graph) {   // captured with another candidate's kernels
@@ -957,12 +961,12 @@ static nb_status autotune(nb_engine *g, int n) {
             // the rhs is made nonzero by setting one value: rho > 0
             const double one = 1.0;
             cudaMemcpyAsync(f + m.npts / 2, &one, sizeof(double), cudaMemcpyHostToDevice, g->stream);
-            st = engine_submit_internal(g, box, n, 0.05, s3, 0.0, 1 << 30, f, tes[ti], &id);
+            st = engine_submit_internal(g, box, n, 0.05, s3, 0.0, 1 << 30, f, tes[ti], &id, false, prec);
             if (st == NB_ERR_OOM) {   // no room for the tuning problem: keep the defaults
                 cudaEventDestroy(a);
                 cudaEventDestroy(b);
                 cudaFree(f);
-                G.lpt = n >= 13 ? 2 : 1;
+                G.lpt = !mixed && n >= 13 ? 2 : 1;
                 G.te = 8;
                 return NB_OK;
             }
@@ -1314,10 +1318,11 @@ nb_status nb_engine_submit(nb_engine *g, const nb_request *req, const double *f_
         if (req->maxit < 0) return fail(NB_ERR_ARG, "maxit must be >= 0");
         if (req->prec != NB_FP64 && req->prec != NB_MIXED) return fail(NB_ERR_ARG, "unknown precision");
         if (((uintptr_t)f_dev & 7u)) return fail(NB_ERR_ARG, "f must be 8-byte aligned");
-        nb_status s = autotune(g, req->n);
+        nb_status s = autotune(g, req->n, (int)req->prec);
         if (s != NB_OK) return s;
-        return engine_submit_internal(g, req->mesh, req->n, req->amp, req->s, req->tol, req->maxit, f_dev,
-                                      g->groups[req->n].te, id_out, false, (int)req->prec, req->inner_tol);
+        const int te = (req->prec == NB_MIXED ? g->mgroups : g->groups)[req->n].te;
+        return engine_submit_internal(g, req->mesh, req->n, req->amp, req->s, req->tol, req->maxit, f_dev, te,
+                                      id_out, false, (int)req->prec, req->inner_tol);
     } catch (...) {
         return fail(NB_ERR_OOM, "engine: host allocation failed");
     }
@@ -1331,10 +1336,11 @@ nb_status nb_engine_submit_unique(nb_engine *g, const nb_request *req, const dou
         if (req->maxit < 0) return fail(NB_ERR_ARG, "maxit must be >= 0");
         if (req->prec != NB_FP64 && req->prec != NB_MIXED) return fail(NB_ERR_ARG, "unknown precision");
         if (((uintptr_t)fu_dev & 7u)) return fail(NB_ERR_ARG, "f must be 8-byte aligned");
-        nb_status s = autotune(g, req->n);
+        nb_status s = autotune(g, req->n, (int)req->prec);
         if (s != NB_OK) return s;
-        return engine_submit_internal(g, req->mesh, req->n, req->amp, req->s, req->tol, req->maxit, fu_dev,
-                                      g->groups[req->n].te, id_out, true, (int)req->prec, req->inner_tol);
+        const int te = (req->prec == NB_MIXED ? g->mgroups : g->groups)[req->n].te;
+        return engine_submit_internal(g, req->mesh, req->n, req->amp, req->s, req->tol, req->maxit, fu_dev, te,
+                                      id_out, true, (int)req->prec, req->inner_tol);
     } catch (...) {
         return fail(NB_ERR_OOM, "engine: host allocation failed");
     }
@@ -1394,10 +1400,12 @@ nb_status nb_engine_stats(const nb_engine *g, size_t *used, size_t *capacity, in
     return NB_OK;
 }
 
-nb_status nb_engine_tuning(const nb_engine *g, int n, int *lines_per_thread, int *elems_per_tile) {
-    if (!g || n < 2 || n > kMaxN) return fail(NB_ERR_ARG, "bad argument");
-    if (lines_per_thread) *lines_per_thread = g->groups[n].lpt;
-    if (elems_per_tile) *elems_per_tile = g->groups[n].te;
+nb_status nb_engine_tuning(const nb_engine *g, int n, nb_precision prec, int *lines_per_thread,
+                           int *elems_per_tile) {
+    if (!g || n < 2 || n > kMaxN || (prec != NB_FP64 && prec != NB_MIXED)) return fail(NB_ERR_ARG, "bad argument");
+    const NGroup &G = prec == NB_MIXED ? g->mgroups[n] : g->groups[n];
+    if (lines_per_thread) *lines_per_thread = G.lpt;
+    if (elems_per_tile) *elems_per_tile = G.te;
     return NB_OK;
 }
 

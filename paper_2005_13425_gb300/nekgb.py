@@ -95,7 +95,7 @@ _SIGS = {
     "nb_engine_request_info": [_vp, ctypes.c_int, _ip, _ip],
     "nb_engine_retire": [_vp, ctypes.c_int, _vp],
     "nb_engine_stats": [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t), _ip],
-    "nb_engine_tuning": [_vp, ctypes.c_int, _ip, _ip],
+    "nb_engine_tuning": [_vp, ctypes.c_int, ctypes.c_int, _ip, _ip],
     "nb_timing_enable": [_vp, ctypes.c_int],
     "nb_timing_read": [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
 }
@@ -404,9 +404,9 @@ def nb_engine_stats(eng):
     return u.value, c.value, a.value
 
 
-def nb_engine_tuning(eng, n: int):
+def nb_engine_tuning(eng, n: int, prec=NB_FP64):
     a, b = ctypes.c_int(0), ctypes.c_int(0)
-    _check(load().nb_engine_tuning(eng, int(n), ctypes.byref(a), ctypes.byref(b)), "nb_engine_tuning")
+    _check(load().nb_engine_tuning(eng, int(n), int(prec), ctypes.byref(a), ctypes.byref(b)), "nb_engine_tuning")
     return a.value, b.value
 
 

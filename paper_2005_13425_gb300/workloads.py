@@ -86,7 +86,7 @@ def batched_run(nekgb, stream, probs, iters=100, sequential=True, prec=0):
             out["sequential_ms"] = seq_ms
             out["sequential_gdofs"] = dofs * iters / (seq_ms * 1e-3) / 1e9
             out["batching_speedup"] = seq_ms / ms
-        out["tuning"] = {n: nekgb.nb_engine_tuning(eng, n) for n in sorted({p["n"] for p in probs})}
+        out["tuning"] = {n: nekgb.nb_engine_tuning(eng, n, prec) for n in sorted({p["n"] for p in probs})}
     finally:
         nekgb.nb_engine_destroy(eng)
     return out

@@ -129,7 +129,7 @@ def test_engine_admission_by_footprint(nek, oracle):
         nek.nb_engine_retire(eng, a)
         st3, c = nek.nb_engine_submit(eng, dims, n, 0.05, s, 1e-8, 100, fd)
         assert st3 == nek.NB_OK
-        lpt, te = nek.nb_engine_tuning(eng, n)
+        lpt, te = nek.nb_engine_tuning(eng, n, nek.NB_FP64)
         assert lpt in (1, 2) and te in (4, 8, 16)
         nek.nb_engine_retire(eng, c)
     finally:
@@ -182,3 +182,19 @@ def test_engine_mixed_footprint_and_budget(nek, oracle):
     P, s, f = problem(oracle, dims, n, 70)
     x, it, rr, st, outer = run_engine(nek, [(dims, n, s, f, 1e-12, 10, nek.NB_MIXED)], iters_per_step=8)[0]
     assert st == nek.NB_ERR_NOT_CONVERGED and 0 < it <= 10 and rr > 1e-12
+
+
+def test_engine_tunes_per_precision(nek, oracle):
+    dims, n = (2, 2, 2), 7
+    _, s, f = problem(oracle, dims, n, 80)
+    eng = nek.nb_engine_create(1 << 30, torch.cuda.current_stream())
+    try:
+        assert nek.nb_engine_tuning(eng, n, nek.NB_MIXED) == (0, 0)        # not used yet
+        st, rid = nek.nb_engine_submit(eng, dims, n, inputs.PERTURB_AMP, s, 1e-8, 1000,
+                                       torch.from_numpy(f).cuda(), prec=nek.NB_MIXED)
+        lpt, te = nek.nb_engine_tuning(eng, n, nek.NB_MIXED)
+        assert lpt == 1 and te in (4, 8, 16)
+        assert nek.nb_engine_tuning(eng, n, nek.NB_FP64) == (0, 0)         # tuned separately
+        nek.nb_engine_retire(eng, rid)
+    finally:
+        nek.nb_engine_destroy(eng)
