@@ -173,7 +173,10 @@ __device__ __forceinline__ void f32_element(const F32ElemIO &io, float beta, flo
 // factors and vectors, so the loads of a whole element are always in
 // flight.  Used for even n up to 10 (n^3 a multiple of 4, so every
 // per-element slab is 16-byte aligned, and two CTAs of 21 n^3 floats fit
-// on an SM).
+// on an SM).  The batched engine stages only at n = 10: there it measured
+// +5.5 % at n = 10 and -7 % at n = 8, where the unstaged kernel's smaller
+// shared memory fits nine CTAs per SM instead of five; the single-problem
+// solve measured faster staged at n = 8 as well (51.5 vs 54.0 ms).
 //
 // Shared memory (floats): stage s at s*f32_stage_floats: G [6n^3] then the
 // vectors (MODE 1: r, p, z; MODE 0: u); after both stages, W0..W2 [3n^3].

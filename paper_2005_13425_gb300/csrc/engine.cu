@@ -419,6 +419,132 @@ eng_m_head(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const in
     }
 }
 
+// The inner head with bulk-copy staging (f32_element_staged): each CTA walks
+// its work items -- the elements of its active tiles, in order -- and
+// while it computes one, the copy engine brings the next one's geometric
+// factors and r, p, z slabs into the other stage, across tile and problem
+// boundaries.  A tile's last element closes the tile's <w,p> partial; a
+// problem's last tile forms alpha.  A copy that does not complete within
+// ~1 s ends the CTA after draining its copies and marks the problem it was
+// on with NB_ERR_TIMEOUT.  Even n <= 10 (16-byte aligned slabs).
+template <int N, int T>
+__global__ void __launch_bounds__(T)
+eng_m_head_staged(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles,
+                  const __grid_constant__ F32Mat<N> D) {
+    constexpr int N3 = N * N * N;
+    constexpr int STAGE = f32_stage_floats<N, 1>();
+    extern __shared__ __align__(16) float smf[];
+    __shared__ double red[32];
+    __shared__ int s_last;
+    __shared__ __align__(8) uint64_t bars[2];
+    const int t = threadIdx.x;
+    const int nt = *ntiles;
+    struct Item {
+        int ti;
+        int64_t e, e1;
+    };
+    // the first active tile at ti or later (stride gridDim.x); the flags of
+    // a tile this CTA has not processed yet cannot change meanwhile (only a
+    // problem's last tile changes them)
+    auto first_from = [&](int ti, Item &it) -> bool {
+        for (; ti < nt; ti += gridDim.x) {
+            const int2 tile = tiles[ti];
+            const ProbDesc &P = desc[tile.x];
+            if (P.phase != kPhaseInner || P.si.done) continue;
+            it.ti = ti;
+            it.e = (int64_t)tile.y * P.te;
+            it.e1 = it.e + P.te < P.m.E ? it.e + P.te : P.m.E;
+            return true;
+        }
+        return false;
+    };
+    auto advance = [&](Item &it) -> bool {
+        if (it.e + 1 < it.e1) {
+            it.e++;
+            return true;
+        }
+        return first_from(it.ti + (int)gridDim.x, it);
+    };
+    Item cur;
+    if (!first_from(blockIdx.x, cur)) return;
+    if (t == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const uint64_t pol = t == 0 ? l2_evict_first_policy() : 0ull;
+    auto issue = [&](const Item &it, int s) {   // thread 0
+        const ProbDesc &P = desc[tiles[it.ti].x];
+        const bool wx = (float)P.si.x_alpha != 0.f;
+        float *st = smf + s * STAGE;
+        mbar_expect_tx(&bars[s], 4u * (wx ? 9 : 8) * N3);
+        bulk_g2s_hint(st, P.g32 + it.e * 6 * N3, 4u * 6 * N3, &bars[s], pol);
+        bulk_g2s(st + 6 * N3, P.r32 + it.e * N3, 4u * N3, &bars[s]);
+        bulk_g2s(st + 7 * N3, P.p32 + it.e * N3, 4u * N3, &bars[s]);
+        if (wx) bulk_g2s_hint(st + 8 * N3, P.z32 + it.e * N3, 4u * N3, &bars[s], pol);
+    };
+    int issued[2] = {1, 0}, waited[2] = {0, 0};
+    if (t == 0) issue(cur, 0);
+    dfa::Acc32 dot;
+    bool ok = true;
+    for (int i = 0;; i++) {
+        const int s = i & 1;
+        Item nxt = cur;
+        const bool more = advance(nxt);
+        if (more) {
+            if (t == 0) issue(nxt, s ^ 1);
+            issued[s ^ 1]++;
+        }
+        ok = __syncthreads_and(mbar_wait(&bars[s], waited[s] & 1)) != 0;
+        if (!ok) break;
+        waited[s]++;
+        const int2 tile = tiles[cur.ti];
+        ProbDesc &P = desc[tile.x];
+        const float beta = P.si.it == 0 ? 0.f : (float)P.si.beta;
+        const float xa = (float)P.si.x_alpha;
+        F32StagedOut o;
+        o.p = P.p32 + cur.e * N3;
+        o.x = P.z32 + cur.e * N3;
+        o.w = P.w32 + cur.e * N3;
+        int ex, ey, ez;
+        element_coords(cur.e, P.m, ex, ey, ez);
+        f32_element_staged<N, 1, T>(smf + s * STAGE, smf + 2 * STAGE, o, beta, xa, ex, ey, ez, P.m, D, dot);
+        if (cur.e + 1 == cur.e1) {   // the tile is complete
+            const double b = block_sum(dot.value(), red);
+            dot = dfa::Acc32();
+            if (t == 0) {
+                P.partials[tile.y] = b;
+                __threadfence();
+                s_last = atomicAdd(&P.si.ticket, 1u) == (unsigned)P.ntile_ax - 1;
+            }
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                double acc = 0.0;
+                for (int k = t; k < P.ntile_ax; k += T) acc += __ldcg(P.partials + k);
+                const double pap = block_sum(acc, red);
+                if (t == 0) {
+                    P.si.ticket = 0;
+                    finalize_alpha(&P.si, pap);
+                    if (P.si.done) P.phase = kPhaseOuter;
+                }
+            }
+            __syncthreads();
+        }
+        if (!more) break;
+        cur = nxt;
+    }
+    if (!ok && t == 0) {   // drain the copies in flight, then report on the current problem
+        for (int s = 0; s < 2; s++)
+            if (issued[s] > waited[s]) mbar_wait(&bars[s], waited[s] & 1);
+        ProbDesc &P = desc[tiles[cur.ti].x];
+        P.sc.status = (int)NB_ERR_TIMEOUT;
+        P.sc.done = 1;
+        P.phase = kPhaseDone;
+    }
+}
+
 // Outer step: shared-node sums of the FP64 w = A x over (slot, node tile)
 // work units (ascending element order, as dssum).  Skipped on the first
 // pass (x = 0, so A x = 0).
@@ -690,6 +816,7 @@ struct nb_engine {
     unsigned long long graph_key = 0;
     int graph_chunk = 0;
     int sms = 1;
+    bool f32_plain = false;   // FP32 heads without bulk staging (NEKGB_F32_STAGED=0)
 };
 
 namespace nekgb {
@@ -785,6 +912,28 @@ static nb_status dispatch_start(nb_engine *g, int n, int slot, int grid) {
 template <int N>
 static nb_status mixed_inner_iteration(nb_engine *g, const NGroup &G) {
     constexpr int T = ax_f32_threads(N);
+    if constexpr (f32_staged_ok<N>() && N == 10) {   // measured faster in batches at n = 10 only
+        if (!g->f32_plain) {
+            const size_t ssm = sizeof(float) * f32_staged_smem_floats<N, 1>();
+            static bool staged_configured = false;
+            if (!staged_configured) {
+                NB_CUDA(cudaFuncSetAttribute(eng_m_head_staged<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)ssm));
+                staged_configured = true;
+            }
+            int occ = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, eng_m_head_staged<N, T>, T, ssm);
+            if (occ < 1) occ = 1;
+            F32Mat<N> D;
+            for (int q = 0; q < N * N; q++) D.d[q] = (float)G.D[q];
+            eng_m_head_staged<N, T><<<g->sms * occ, T, ssm, g->stream>>>(g->d_desc, G.d_ax, G.d_cnt, D);
+            NB_LAUNCH_CHECK("eng_m_head_staged");
+            eng_assemble<float, N, true><<<g->sms * 5, kEngThreads, 0, g->stream>>>(g->d_desc, G.d_ax, G.d_ds,
+                                                                                  G.d_cnt);
+            NB_LAUNCH_CHECK("eng_assemble<mixed>");
+            return NB_OK;
+        }
+    }
     const size_t smem = sizeof(float) * f32_smem_floats(N);
     static bool configured = false;
     if (!configured) {
@@ -1257,6 +1406,10 @@ nb_status nb_engine_create(nb_engine **out, size_t arena_bytes, void *cuda_strea
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
+        {
+            const char *st = getenv("NEKGB_F32_STAGED");
+            g->f32_plain = st && st[0] == '0';
+        }
         cudaError_t e = dev_alloc((void **)&g->arena.base, arena_bytes);
         if (e != cudaSuccess) { delete g; return cuda_fail(e, "engine: arena"); }
         g->arena.cap = arena_bytes;

@@ -198,3 +198,28 @@ def test_engine_tunes_per_precision(nek, oracle):
         nek.nb_engine_retire(eng, rid)
     finally:
         nek.nb_engine_destroy(eng)
+
+
+def test_engine_staged_f32_head_matches_plain(nek, oracle):
+    """The bulk-copy staged FP32 head (n = 10) and the plain one give
+    bit-identical mixed solves; the staged one crosses tile and problem
+    boundaries (several problems of the same n)."""
+    import os
+    items = []
+    for pid, (dims, n) in enumerate([((3, 2, 2), 10), ((2, 2, 3), 10), ((5, 3, 2), 10)]):
+        _, s, f = problem(oracle, dims, n, 90 + pid)
+        items.append((dims, n, s, f, 1e-10, 20000, nek.NB_MIXED))
+    outs = []
+    for staged in ("1", "0"):
+        old = os.environ.get("NEKGB_F32_STAGED")
+        os.environ["NEKGB_F32_STAGED"] = staged
+        try:
+            outs.append(run_engine(nek, items, iters_per_step=32))
+        finally:
+            if old is None:
+                del os.environ["NEKGB_F32_STAGED"]
+            else:
+                os.environ["NEKGB_F32_STAGED"] = old
+    for a, b in zip(*outs):
+        assert a[1] == b[1] and a[2] == b[2] and a[4] == b[4] and a[3] == nek.NB_OK
+        assert np.array_equal(a[0], b[0])
