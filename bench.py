@@ -2,12 +2,22 @@
 
 A step is one fixed-iteration CG solve (500 iterations, tol <= 0) of the
 synthetic Nekbone box problem with E = 4096 elements (16 x 16 x 16) and
-n = 10 GLL points per direction (degree 9), FP64: every iteration runs ax_e
-fused with p = r + beta p, dssum, mask, <w,p>_c and the x/r update with
-<r,r>_c.  The metric is Ax throughput in GDOF/s: local points (E n^3) times
-CG iterations, divided by the device time.  The working set (gxyz 197 MB +
-five 33 MB vectors) is larger than the 129 MB L2, so no flush is needed
-between iterations; the standalone ax_e timings below flush L2.
+n = 10 GLL points per direction (degree 9), FP64-accurate: every iteration
+runs the ax_e head (x += alpha p, p = r + beta p, w = ax_e(p), mask,
+<w,p>_c, alpha) and the fused dssum + r update (<r,r>_c, beta).  The metric
+is Ax throughput in GDOF/s: local points (E n^3) times CG iterations,
+divided by the device time.  The working set (gxyz pairs 197 MB + four
+33 MB vectors) is larger than the 129 MB L2, so no flush is needed between
+iterations; the standalone ax_e timings below flush L2.
+
+The JSON line adds: `e2e` (the same solve through nb_cg_solve_host with
+pinned host buffers, copies timed), `roofline` / `roofline_other` (the CG
+head against the FP32-instruction ALU bound and the measured HBM peak, with
+the DRAM traffic recorded in profiles/ for the same kernel sources),
+`mixed_vs_fp64` (time to relres 1e-10, FP64 vs mixed, n = 8 and 10),
+`batched` / `batched_mixed` and `serving` (the engine, FP64 and mixed),
+`clocks` (nvidia-smi during the timed region) and `cpu_baseline` (the
+oracle on the host cores).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 N > 1 runs under torchrun as independent replicas (weak scaling): each rank
