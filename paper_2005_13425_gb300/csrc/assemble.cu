@@ -6,8 +6,9 @@
 // With <w,p>_c summed by the head as local products (p is continuous), alpha
 // is known before dssum.  The assembled w is then needed only to update r,
 // so this kernel never writes w back:
-//  * points of an element that lie on no shared face have one copy:
-//    r -= alpha w there;
+//  * element-interior points have one copy: r -= alpha w there.  The other
+//    single-copy points lie on box faces, where the Dirichlet mask keeps w
+//    (zeroed by the head) and r at +0.0, so they are left alone;
 //  * every shared node gathers its copies of w in ascending element order
 //    (the dssum order, so the sum is the one dssum writes), updates r once
 //    (r is continuous: every copy holds the same value) and writes the new
@@ -36,7 +37,6 @@ assemble_update_kernel(T *__restrict__ r, const T *__restrict__ w, Mesh m, DsCat
     if (sc->done) return;
     constexpr bool F32 = std::is_same<T, float>::value;
     constexpr int N3 = N * N * N;
-    constexpr int K = (N3 + kAsmThreads - 1) / kAsmThreads;
     const T alpha = (T)sc->alpha;
     const int erb = (int)((__double_as_longlong(sc->rr) >> 52) & 0x7ff);
     const int sh = erb == 0 ? 0 : -((erb - 1023) >> 1);
@@ -50,26 +50,27 @@ assemble_update_kernel(T *__restrict__ r, const T *__restrict__ w, Mesh m, DsCat
             sq.add_sq(v.x, v.y, 1.f);
         }
     };
-    // single-copy points, element by element
-    unsigned pf[K];
+    // element-interior points, element by element
+    if constexpr (N > 2) {
+        constexpr int NI = N - 2, NI3 = NI * NI * NI;
+        constexpr int KI = (NI3 + kAsmThreads - 1) / kAsmThreads;
+        int qk[KI];
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-        const int q = threadIdx.x + k * kAsmThreads;
-        pf[k] = q < N3 ? point_faces<N>(q) : 0u;
-    }
-    for (int64_t e = blockIdx.x; e < m.E; e += gridDim.x) {
-        int ex, ey, ez;
-        element_coords(e, m, ex, ey, ez);
-        const unsigned sf = shared_faces(ex, ey, ez, m);
-        const int64_t base = e * N3;
+        for (int k = 0; k < KI; k++) {
+            const int qi = threadIdx.x + k * kAsmThreads;
+            const int a = qi % NI, b = (qi / NI) % NI, c = qi / (NI * NI);
+            qk[k] = (1 + a) + N * (1 + b) + N * N * (1 + c);
+        }
+        for (int64_t e = blockIdx.x; e < m.E; e += gridDim.x) {
+            const int64_t base = e * N3;
 #pragma unroll
-        for (int k = 0; k < K; k++) {
-            const int q = threadIdx.x + k * kAsmThreads;
-            if (K * kAsmThreads != N3 && q >= N3) break;
-            if (pf[k] & sf) continue;   // a shared node: below
-            const T rn = fma(-alpha, __ldcs(w + base + q), r[base + q]);
-            r[base + q] = rn;
-            add_sq(rn);
+            for (int k = 0; k < KI; k++) {
+                if (KI * kAsmThreads != NI3 && threadIdx.x + k * kAsmThreads >= NI3) break;
+                const int64_t q = base + qk[k];
+                const T rn = fma(-alpha, __ldcs(w + q), r[q]);
+                r[q] = rn;
+                add_sq(rn);
+            }
         }
     }
     // shared nodes

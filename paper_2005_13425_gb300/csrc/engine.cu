@@ -131,8 +131,8 @@ eng_ax_head(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const i
 }
 
 // Second kernel of an engine CG iteration (as assemble.cu for one
-// problem): over the element tiles, r -= alpha w at points on no shared
-// face; over the node tiles, each shared node gathers its copies of w in the
+// problem): over the element tiles, r -= alpha w at the element-interior
+// points; over the node tiles, each shared node gathers its copies of w in the
 // dssum order, updates r once and writes it to every copy.  <r,r>_c is
 // summed over unique nodes; the problem's last tile forms rho, beta and the
 // convergence decision (MIXED: of the inner FP32 solve, which hands the
@@ -142,14 +142,15 @@ __global__ void __launch_bounds__(kEngThreads, 5)
 eng_assemble(ProbDesc *__restrict__ desc, const int2 *__restrict__ ax_tiles, const int2 *__restrict__ ds_tiles,
              const int *__restrict__ cnt) {
     constexpr int N3 = N * N * N;
-    constexpr int K = (N3 + kEngThreads - 1) / kEngThreads;
+    constexpr int NI = N > 2 ? N - 2 : 1, NI3 = N > 2 ? NI * NI * NI : 0;
+    constexpr int KI = (NI3 + kEngThreads - 1) / kEngThreads;
     __shared__ double red[32];
     __shared__ int s_last;
-    unsigned pf[K];
+    int qk[KI > 0 ? KI : 1];   // this thread's element-interior points
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-        const int q = threadIdx.x + k * kEngThreads;
-        pf[k] = q < N3 ? point_faces<N>(q) : 0u;
+    for (int k = 0; k < KI; k++) {
+        const int qi = threadIdx.x + k * kEngThreads;
+        qk[k] = (1 + qi % NI) + N * (1 + (qi / NI) % NI) + N * N * (1 + qi / (NI * NI));
     }
     const int nax = cnt[0], nds = cnt[1];
     for (int ti = blockIdx.x; ti < nax + nds; ti += gridDim.x) {
@@ -180,22 +181,20 @@ eng_assemble(ProbDesc *__restrict__ desc, const int2 *__restrict__ ax_tiles, con
                 sq.add_sq(v.x, v.y, 1.f);
             }
         };
-        if (el) {
-            const int64_t e0 = (int64_t)tile.y * P.te;
-            const int64_t e1 = e0 + P.te < m.E ? e0 + P.te : m.E;
-            for (int64_t e = e0; e < e1; e++) {
-                int ex, ey, ez;
-                element_coords(e, m, ex, ey, ez);
-                const unsigned sf = shared_faces(ex, ey, ez, m);
-                const int64_t base = e * N3;
+        if (el) {   // element-interior points (box-face points stay +0.0, see assemble.cu)
+            if constexpr (N > 2) {
+                const int64_t e0 = (int64_t)tile.y * P.te;
+                const int64_t e1 = e0 + P.te < m.E ? e0 + P.te : m.E;
+                for (int64_t e = e0; e < e1; e++) {
+                    const int64_t base = e * N3;
 #pragma unroll
-                for (int k = 0; k < K; k++) {
-                    const int q = threadIdx.x + k * kEngThreads;
-                    if (K * kEngThreads != N3 && q >= N3) break;
-                    if (pf[k] & sf) continue;
-                    const T rn = fma(-alpha, __ldcs(w + base + q), r[base + q]);
-                    r[base + q] = rn;
-                    add_sq(rn);
+                    for (int k = 0; k < KI; k++) {
+                        if (KI * kEngThreads != NI3 && threadIdx.x + k * kEngThreads >= NI3) break;
+                        const int64_t q = base + qk[k];
+                        const T rn = fma(-alpha, __ldcs(w + q), r[q]);
+                        r[q] = rn;
+                        add_sq(rn);
+                    }
                 }
             }
         } else {
