@@ -346,7 +346,8 @@ typedef enum {
     NB_K_DSSUM = 1,   /* dssum (+ mask in the solver) */
     NB_K_MASK = 2,
     NB_K_DOT = 3,     /* weighted dot products and their finalisation */
-    NB_K_UPDATE = 4,  /* CG x/r updates + <r,r>_c */
+    NB_K_UPDATE = 4,  /* CG r update + <r,r>_c (in the two-kernel iteration
+                         fused with dssum) */
     NB_K_OTHER = 5,
     NB_K_COUNT = 6
 } nb_kernel_id;

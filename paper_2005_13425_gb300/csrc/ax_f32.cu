@@ -28,7 +28,8 @@ struct AxF32Args {
 };
 
 // MODE 0: w = ax_e(u).  MODE 1: inner CG head (x += x_alpha p, p = r + beta
-// p, w = ax_e(p), box faces zeroed, element-interior <w,p> per CTA).
+// p, w = ax_e(p), box faces zeroed, the local products w p per CTA; with
+// finalize the last CTA forms alpha).
 template <int N, int MODE>
 __global__ void __launch_bounds__(ax_f32_threads(N))
 ax_f32_kernel(AxF32Args a, const __grid_constant__ F32Mat<N> D) {

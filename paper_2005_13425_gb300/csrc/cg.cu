@@ -5,18 +5,20 @@
 //
 // Every scalar of the iteration (rho, alpha, beta, <w,p>_c) lives on the
 // device and reductions are deterministic (reduce.cuh).  With the box mask
-// one iteration is three kernels:
+// and no preconditioner one iteration is two kernels:
 //   1. ax_e head: x += alpha_prev p (the x update owed by the previous
 //      iteration), p = r + beta p, w = ax_e(p), w := 0 on box faces, and
 //      <w,p>_c as the sum of the local products w p (p is continuous, so
-//      sum_g (sum_copies w) p_g equals the sum over local points);
-//   2. dssum of w; its last CTA forms alpha = rho/<w,p>_c;
-//   3. r -= alpha w with <r,r>_c; its last CTA forms rho, beta and the
-//      convergence decision.
-// The last owed x update runs once after the loop.  With a caller-supplied
-// mask array the mask may select any point, so the iteration falls back to
-// separate dssum, mask and <w,p>_c kernels.  Chunks of iterations are
-// captured as CUDA graphs; every kernel returns at once when `done` is set.
+//      sum_g (sum_copies w) p_g equals the sum over local points); its last
+//      CTA forms alpha = rho/<w,p>_c;
+//   2. assemble_update (assemble.cu): dssum fused with r -= alpha w and
+//      <r,r>_c; its last CTA forms rho, beta and the convergence decision.
+// With the Jacobi preconditioner the dssum (forming alpha) and the update
+// (with <r,z>_c) are separate kernels.  The last owed x update runs once
+// after the loop.  With a caller-supplied mask array the mask may select
+// any point, so the iteration falls back to separate dssum, mask and
+// <w,p>_c kernels.  Chunks of iterations are captured as CUDA graphs; every
+// kernel returns at once when `done` is set.
 #include <math.h>
 
 #include <mutex>

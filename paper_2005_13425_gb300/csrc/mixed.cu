@@ -11,8 +11,9 @@
 //         d = CG_fp32(A, r) to a relative inner residual (1e-4 by default)
 //         x += d (FP64)
 //
-// The inner CG is the fused three-kernel iteration of the FP64 solver on
-// FP32 vectors: dot products accumulate in FP64 and all scalars are FP64
+// The inner CG is the two-kernel iteration of the FP64 solver on FP32
+// vectors (the FP32 head, then assemble_update): dot products accumulate
+// with compensated FP32 sums into FP64 partials, and all scalars are FP64
 // on the device.
 #include <math.h>
 #include <stdlib.h>
