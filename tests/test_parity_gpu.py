@@ -288,6 +288,25 @@ def test_cg_fixed_iterations_across_n(nek, oracle, dims, n):
     assert rel_err(xg, x_ref) <= 1e-8
 
 
+def test_full_size_cg_in_bench_configuration(nek, oracle):
+    """E = 4096, n = 10, the benchmark's problem and launch path (device-built
+    geometry, graph-captured two-kernel iteration): 20 fixed CG iterations
+    against the oracle's CG on the same mesh and right-hand side."""
+    dims, n = (16, 16, 16), 10
+    s = inputs.perturbation_coeffs(inputs.SEED_MESH)
+    P = oracle.box_problem(*dims, n, inputs.PERTURB_AMP, s)
+    f = oracle.apply_mask(P["mask"], oracle.scatter_unique(*dims, n, inputs.unique_field(*dims, n, inputs.SEED_F)))
+    x_ref, it_ref, rr_ref, hist_ref, st = oracle.cg(*dims, n, P["D"], P["gxyz"], P["mask"], f, tol=0.0, maxit=20)
+    with Ctx(nek, dims, n, inputs.PERTURB_AMP, s, box=True) as ctx:
+        x = torch.zeros(P["E"], n ** 3, dtype=torch.float64, device="cuda")
+        st, it, rr = nek.nb_cg_solve(ctx, dev(f), x, tol=0.0, maxit=20)
+        xg = host(x)
+        hist = nek.nb_cg_history(ctx)
+    assert it == 20 == it_ref
+    assert np.abs(hist - hist_ref).max() / hist_ref.max() <= 1e-8
+    assert rel_err(xg, x_ref) <= 1e-8
+
+
 def test_cg_tolerance_and_determinism(nek, oracle):
     dims, n = (3, 2, 2), 6
     P, f = cg_inputs(oracle, dims, n, seed_mesh=3, seed_f=4)
