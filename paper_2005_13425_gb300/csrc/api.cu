@@ -3,6 +3,9 @@
 // and solver kernels live in the other translation units.
 #include <stdio.h>
 #include <stdlib.h>
+
+#include <mutex>
+#include <set>
 #include <string.h>
 
 #include <atomic>
@@ -26,6 +29,18 @@ nb_status fail(nb_status s, const std::string &msg) {
 nb_status cuda_fail(cudaError_t e, const char *what) {
     set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
     return e == cudaErrorMemoryAllocation ? NB_ERR_OOM : NB_ERR_CUDA;
+}
+
+nb_status smem_attr(const void *kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({kernel, dev})) return NB_OK;
+    NB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    done.insert({kernel, dev});
+    return NB_OK;
 }
 
 cudaError_t dev_alloc(void **p, size_t bytes) {

@@ -153,7 +153,6 @@ template <int N, bool EO>
 static nb_status launch_df_nv(nb_ctx *c, const double *u, double *w, int mode) {
     constexpr int T = ax_df_threads(N);
     const size_t smem = sizeof(float2) * 6 * N * N * N;
-    static bool configured[2] = {false, false};
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -179,9 +178,9 @@ static nb_status launch_df_nv(nb_ctx *c, const double *u, double *w, int mode) {
     }
     args.m = c->m;
     auto kern = mode == 0 ? ax_df_kernel<N, 0, EO> : ax_df_kernel<N, 1, EO>;
-    if (!configured[mode]) {
-        NB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured[mode] = true;
+    {
+        const nb_status s = set_smem(kern, smem);
+        if (s != NB_OK) return s;
     }
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, smem);
     if (occ < 1) occ = 1;

@@ -166,7 +166,6 @@ template <int N>
 static nb_status launch_f32_n(nb_ctx *c, const float *u, float *w, int mode) {
     constexpr int T = ax_f32_threads(N);
     const size_t smem = sizeof(float) * f32_smem_floats(N);
-    static bool configured[2] = {false, false};
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -193,10 +192,9 @@ static nb_status launch_f32_n(nb_ctx *c, const float *u, float *w, int mode) {
             auto kern = mode == 0 ? ax_f32_staged_kernel<N, 0> : ax_f32_staged_kernel<N, 1>;
             const size_t ssm = sizeof(float) * (mode == 0 ? f32_staged_smem_floats<N, 0>()
                                                           : f32_staged_smem_floats<N, 1>());
-            static bool staged_configured[2] = {false, false};
-            if (!staged_configured[mode]) {
-                NB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
-                staged_configured[mode] = true;
+            {
+                const nb_status s = set_smem(kern, ssm);
+                if (s != NB_OK) return s;
             }
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, ssm);
             if (occ < 1) occ = 1;
@@ -210,9 +208,9 @@ static nb_status launch_f32_n(nb_ctx *c, const float *u, float *w, int mode) {
         }
     }
     auto kern = mode == 0 ? ax_f32_kernel<N, 0> : ax_f32_kernel<N, 1>;
-    if (!configured[mode]) {
-        NB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured[mode] = true;
+    {
+        const nb_status s = set_smem(kern, smem);
+        if (s != NB_OK) return s;
     }
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, T, smem);
     if (occ < 1) occ = 1;

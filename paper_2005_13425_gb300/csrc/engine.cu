@@ -855,10 +855,9 @@ template <int N, int LPT>
 static nb_status head_launch(nb_engine *g, const NGroup &G) {
     constexpr int T = df_threads_lpt(N, LPT);
     const size_t smem = sizeof(float2) * 6 * N * N * N;
-    static bool configured = false;
-    if (!configured) {
-        NB_CUDA(cudaFuncSetAttribute(eng_ax_head<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured = true;
+    {
+        const nb_status s = set_smem(eng_ax_head<N, T>, smem);
+        if (s != NB_OK) return s;
     }
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, eng_ax_head<N, T>, T, smem);
@@ -914,11 +913,9 @@ static nb_status mixed_inner_iteration(nb_engine *g, const NGroup &G) {
     if constexpr (f32_staged_ok<N>() && N == 10) {   // measured faster in batches at n = 10 only
         if (!g->f32_plain) {
             const size_t ssm = sizeof(float) * f32_staged_smem_floats<N, 1>();
-            static bool staged_configured = false;
-            if (!staged_configured) {
-                NB_CUDA(cudaFuncSetAttribute(eng_m_head_staged<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)ssm));
-                staged_configured = true;
+            {
+                const nb_status s = set_smem(eng_m_head_staged<N, T>, ssm);
+                if (s != NB_OK) return s;
             }
             int occ = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, eng_m_head_staged<N, T>, T, ssm);
@@ -934,10 +931,9 @@ static nb_status mixed_inner_iteration(nb_engine *g, const NGroup &G) {
         }
     }
     const size_t smem = sizeof(float) * f32_smem_floats(N);
-    static bool configured = false;
-    if (!configured) {
-        NB_CUDA(cudaFuncSetAttribute(eng_m_head<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured = true;
+    {
+        const nb_status s = set_smem(eng_m_head<N, T>, smem);
+        if (s != NB_OK) return s;
     }
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, eng_m_head<N, T>, T, smem);
@@ -955,10 +951,9 @@ template <int N>
 static nb_status mixed_outer_pass(nb_engine *g, const NGroup &G) {
     constexpr int T = ax_df_threads(N);
     const size_t smem = sizeof(float2) * 6 * N * N * N;
-    static bool configured = false;
-    if (!configured) {
-        NB_CUDA(cudaFuncSetAttribute(eng_m_outer_ax<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured = true;
+    {
+        const nb_status s = set_smem(eng_m_outer_ax<N, T>, smem);
+        if (s != NB_OK) return s;
     }
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, eng_m_outer_ax<N, T>, T, smem);

@@ -35,6 +35,14 @@ nb_status cuda_fail(cudaError_t e, const char *what);
 // paths can be tested without touching the GPU.
 cudaError_t dev_alloc(void **p, size_t bytes);
 
+// Allow `bytes` of dynamic shared memory for a kernel on the current device
+// (set once per kernel and device; thread-safe).
+nb_status smem_attr(const void *kernel, size_t bytes);
+template <typename K>
+inline nb_status set_smem(K *kernel, size_t bytes) {
+    return smem_attr(reinterpret_cast<const void *>(kernel), bytes);
+}
+
 // ---------------------------------------------------------------- mesh
 // Everything a kernel needs to know about the box topology.
 struct Mesh {
