@@ -123,12 +123,7 @@ static void free_ctx(nb_ctx *c) {
 static nb_status new_ctx(nb_ctx **out, nb_box mesh, int n, nb_precision prec, void *stream) {
     nb_ctx *c = new (std::nothrow) nb_ctx();
     if (!c) return fail(NB_ERR_OOM, "host allocation of the context failed");
-    c->m.ex = mesh.ex; c->m.ey = mesh.ey; c->m.ez = mesh.ez; c->m.n = n;
-    c->m.E = (int64_t)mesh.ex * mesh.ey * mesh.ez;
-    c->m.npts = c->m.E * n * n * n;
-    c->m.NX = (int64_t)mesh.ex * (n - 1) + 1;
-    c->m.NY = (int64_t)mesh.ey * (n - 1) + 1;
-    c->m.NZ = (int64_t)mesh.ez * (n - 1) + 1;
+    c->m = make_box_mesh(mesh.ex, mesh.ey, mesh.ez, n);
     c->prec = prec;
     c->stream = (cudaStream_t)stream;
     c->ax_variant = 0;
@@ -388,13 +383,7 @@ nb_status nb_dot_c_noalloc(nb_box mesh, int n, const double *a, const double *b,
     if (s != NB_OK) return s;
     if (!a || !b || !out) return fail(NB_ERR_ARG, "NULL argument");
     if (!aligned8(a) || !aligned8(b) || !aligned8(out)) return fail(NB_ERR_ARG, "pointers must be 8-byte aligned");
-    Mesh m;
-    m.ex = mesh.ex; m.ey = mesh.ey; m.ez = mesh.ez; m.n = n;
-    m.E = (int64_t)mesh.ex * mesh.ey * mesh.ez;
-    m.npts = m.E * n * n * n;
-    m.NX = (int64_t)mesh.ex * (n - 1) + 1;
-    m.NY = (int64_t)mesh.ey * (n - 1) + 1;
-    m.NZ = (int64_t)mesh.ez * (n - 1) + 1;
+    const Mesh m = make_box_mesh(mesh.ex, mesh.ey, mesh.ez, n);
     return dot_c_noalloc(m, a, b, out, (cudaStream_t)cuda_stream);
     NB_GUARD_END
 }

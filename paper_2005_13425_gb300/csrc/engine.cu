@@ -839,16 +839,7 @@ static size_t desc_footprint(const Mesh &m, int prec, size_t *parts) {
     return parts[0] + 4 * parts[1] + parts[2];
 }
 
-static Mesh make_mesh(nb_box b, int n) {
-    Mesh m;
-    m.ex = b.ex; m.ey = b.ey; m.ez = b.ez; m.n = n;
-    m.E = (int64_t)b.ex * b.ey * b.ez;
-    m.npts = m.E * n * n * n;
-    m.NX = (int64_t)b.ex * (n - 1) + 1;
-    m.NY = (int64_t)b.ey * (n - 1) + 1;
-    m.NZ = (int64_t)b.ez * (n - 1) + 1;
-    return m;
-}
+static Mesh make_mesh(nb_box b, int n) { return make_box_mesh(b.ex, b.ey, b.ez, n); }
 
 // ---- kernel dispatch over (N, LPT)
 template <int N, int LPT>

@@ -49,7 +49,28 @@ struct Mesh {
     int ex, ey, ez, n;
     int64_t E, npts;
     int64_t NX, NY, NZ;
+    // exact reciprocals for element id -> (ex, ey, ez): ceil(2^64 / d) for
+    // d = ex and d = ex ey (0 when d = 1); see make_box_mesh
+    unsigned long long inv_ex, inv_exy;
 };
+
+// The box mesh of ex x ey x ez elements with n points per direction.
+// floor(q / d) = floor(q ceil(2^64 / d) / 2^64) for every 32-bit q and
+// d >= 2 (Granlund and Montgomery, 1994), so element coordinates need one
+// multiply-high per division.
+inline Mesh make_box_mesh(int ex, int ey, int ez, int n) {
+    Mesh m;
+    m.ex = ex; m.ey = ey; m.ez = ez; m.n = n;
+    m.E = (int64_t)ex * ey * ez;
+    m.npts = m.E * n * n * n;
+    m.NX = (int64_t)ex * (n - 1) + 1;
+    m.NY = (int64_t)ey * (n - 1) + 1;
+    m.NZ = (int64_t)ez * (n - 1) + 1;
+    auto recip = [](unsigned long long d) { return d <= 1 ? 0ull : (~0ull / d) + 1ull; };
+    m.inv_ex = recip((unsigned long long)ex);
+    m.inv_exy = recip((unsigned long long)ex * ey);
+    return m;
+}
 
 // ---------------------------------------------------------------- CG state
 // Device-resident scalars of one CG solve.

@@ -126,14 +126,17 @@ __device__ __forceinline__ unsigned box_faces(int ex, int ey, int ez, const Mesh
            ((unsigned)(ey == m.ey - 1) << 3) | ((unsigned)(ez == 0) << 4) | ((unsigned)(ez == m.ez - 1) << 5);
 }
 
-// Element id -> (ex, ey, ez) with 32-bit arithmetic.
+// Element id -> (ex, ey, ez): two multiply-high divisions by the mesh's
+// exact reciprocals (make_box_mesh).
 __device__ __forceinline__ void element_coords(int64_t e, const Mesh &m, int &ex, int &ey, int &ez) {
-    const int ei = (int)e;
-    const int exy = m.ex * m.ey;
-    ez = ei / exy;
-    const int r = ei - ez * exy;
-    ey = r / m.ex;
-    ex = r - ey * m.ex;
+    const unsigned ei = (unsigned)e;
+    const unsigned exy = (unsigned)(m.ex * m.ey);
+    const unsigned z = m.inv_exy ? (unsigned)__umul64hi((unsigned long long)ei, m.inv_exy) : ei;
+    const unsigned r = ei - z * exy;
+    const unsigned y = m.inv_ex ? (unsigned)__umul64hi((unsigned long long)r, m.inv_ex) : r;
+    ez = (int)z;
+    ey = (int)y;
+    ex = (int)(r - y * (unsigned)m.ex);
 }
 
 }  // namespace nekgb
