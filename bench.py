@@ -14,6 +14,8 @@ The JSON line adds: `e2e` (the same solve through nb_cg_solve_host with
 pinned host buffers, copies timed), `roofline` / `roofline_other` (the CG
 head against the FP32-instruction ALU bound and the measured HBM peak, with
 the DRAM traffic recorded in profiles/ for the same kernel sources),
+`ax_sweep_n10` (ax_e alone and with dssum, L2 flushed, and the CG iteration
+time at E = 1024, 2048 and 4096),
 `mixed_vs_fp64` (time to relres 1e-10, FP64 vs mixed, n = 8 and 10),
 `batched` / `batched_mixed` and `serving` (the engine, FP64 and mixed),
 `clocks` (nvidia-smi during the timed region) and `cpu_baseline` (the
@@ -396,6 +398,40 @@ def run_gpu(args, rank, world, local):
     t_ax_fp64 = timed(lambda: nekgb.nb_ax(ctx, u, w), reps=5)
     nekgb.nb_set_ax_variant(ctx, variant_default)
 
+    # ---- the Ax sweep over E = 1024, 2048, 4096 (n = 10): ax_e alone and
+    # ax_e + dssum with L2 flushed (median of 20), and the per-iteration time
+    # of a 500-iteration CG solve
+    sweep = []
+    for dims in ((16, 8, 8), (16, 16, 8), DIMS):
+        Es = dims[0] * dims[1] * dims[2]
+        Ds = Es * NGLL ** 3
+        cs = nekgb.nb_setup_box(dims, NGLL, inputs.PERTURB_AMP, s, nekgb.NB_FP64, stream)
+        try:
+            us = torch.from_numpy(inputs.local_field(Es, NGLL, inputs.SEED_U)).cuda()
+            ws = torch.empty_like(us)
+            nekgb.nb_ax(cs, us, ws)
+            ta = timed(lambda: nekgb.nb_ax(cs, us, ws))
+            tad = timed(lambda: (nekgb.nb_ax(cs, us, ws), nekgb.nb_dssum(cs, ws)))
+            fus = torch.from_numpy(inputs.unique_field(*dims, NGLL, inputs.SEED_F)).cuda()
+            fs = torch.empty(Es, NGLL ** 3, dtype=torch.float64, device="cuda")
+            nekgb.nb_scatter_unique(cs, fus, fs)
+            nekgb.nb_mask(cs, fs)
+            xs = torch.zeros_like(fs)
+            nekgb.nb_cg_solve(cs, fs, xs, tol=0.0, maxit=CG_ITERS)
+            xs.zero_()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            nekgb.nb_cg_solve(cs, fs, xs, tol=0.0, maxit=CG_ITERS)
+            c1.record(stream)
+            c1.synchronize()
+            tcg = c0.elapsed_time(c1) / CG_ITERS
+            sweep.append({"E": Es, "mesh": "x".join(map(str, dims)), "ax_ms": ta,
+                          "ax_gdofs": Ds / (ta * 1e-3) / 1e9, "ax_dssum_ms": tad,
+                          "ax_dssum_gdofs": Ds / (tad * 1e-3) / 1e9,
+                          "cg_iteration_ms": tcg, "cg_gdofs": Ds / (tcg * 1e-3) / 1e9})
+        finally:
+            nekgb.nb_destroy(cs)
+
     # ---- roofline of the dominant kernel, from the timed region's events
     hbm, _, peak_src = metrics.measured_peaks(ROOT)
     ax = kern["ax_e"]
@@ -458,6 +494,7 @@ def run_gpu(args, rank, world, local):
                     "hbm_frac": metrics.ax_bytes_per_point(8) * D / (t_ax * 1e-3) / 1e9 / hbm,
                     "l2": "flushed between reps"},
         "ax_dssum": {"ms": t_axds, "gdofs": D / (t_axds * 1e-3) / 1e9},
+        "ax_sweep_n10": sweep,
         "ax_only_native_fp64": {"ms": t_ax_fp64, "gdofs": D / (t_ax_fp64 * 1e-3) / 1e9,
                                 "fp64_tflops": metrics.ax_flops_per_point(NGLL) * D / (t_ax_fp64 * 1e-3) / 1e12},
         "e2e": {"value": value_e2e, "unit": "GDOF/s",

@@ -5,7 +5,7 @@
 #include <stdlib.h>
 
 #include <mutex>
-#include <set>
+#include <map>
 #include <string.h>
 
 #include <atomic>
@@ -33,14 +33,27 @@ nb_status cuda_fail(cudaError_t e, const char *what) {
 
 nb_status smem_attr(const void *kernel, size_t bytes) {
     static std::mutex mu;
-    static std::set<std::pair<const void *, int>> done;
+    static std::map<std::pair<const void *, int>, size_t> done;   // largest size set
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(mu);
-    if (done.count({kernel, dev})) return NB_OK;
+    const auto it = done.find({kernel, dev});
+    if (it != done.end() && it->second >= bytes) return NB_OK;
     NB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    done.insert({kernel, dev});
+    done[{kernel, dev}] = bytes;
     return NB_OK;
+}
+
+int device_sms() {
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int v = dev >= 0 && dev < kMaxDev ? cache[dev].load(std::memory_order_relaxed) : 0;
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 1;
+    if (dev >= 0 && dev < kMaxDev) cache[dev].store(v, std::memory_order_relaxed);
+    return v;
 }
 
 cudaError_t dev_alloc(void **p, size_t bytes) {

@@ -118,14 +118,7 @@ assemble_update_kernel(T *__restrict__ r, const T *__restrict__ w, Mesh m, DsCat
 }
 
 static int asm_grid(const nb_ctx *c) {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms < 1) sms = 1;
-    }
-    const int64_t cap = (int64_t)sms * 5;
+    const int64_t cap = (int64_t)device_sms() * 5;
     return (int)(c->m.E < cap ? c->m.E : cap);
 }
 

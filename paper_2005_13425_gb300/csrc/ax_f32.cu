@@ -166,9 +166,8 @@ template <int N>
 static nb_status launch_f32_n(nb_ctx *c, const float *u, float *w, int mode) {
     constexpr int T = ax_f32_threads(N);
     const size_t smem = sizeof(float) * f32_smem_floats(N);
-    int dev = 0, sms = 0, occ = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int occ = 0;
+    const int sms = device_sms();
     F32Mat<N> D;
     for (int q = 0; q < N * N; q++) D.d[q] = (float)c->D_host[q];
     AxF32Args args{};

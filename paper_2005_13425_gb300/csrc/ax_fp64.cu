@@ -151,9 +151,8 @@ ax_fp64_kernel(const double *__restrict__ u, double *__restrict__ w,
 template <int N>
 static nb_status launch_n(nb_ctx *c, const double *u, double *w, int mode) {
     const int threads = ((N * N + 31) / 32) * 32;
-    int dev = 0, sms = 0, occ = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int occ = 0;
+    const int sms = device_sms();
     if (mode == 0)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ax_fp64_kernel<N, 0>, threads, 0);
     else

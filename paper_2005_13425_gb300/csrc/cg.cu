@@ -41,16 +41,7 @@ int dssum_grid(const nb_ctx *c);
 constexpr int kRedThreads = 256;
 constexpr int kMaxRedGrid = 16384;   // partial slots reserved per reduction
 
-static int sms() {
-    static int v = 0;
-    if (!v) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        if (v < 1) v = 1;
-    }
-    return v;
-}
+static int sms() { return device_sms(); }
 
 // Four CTAs per SM, each striding over many elements: every CTA ends with
 // one block reduction (~1.5k FP64 adds), so few, long-lived CTAs keep that

@@ -1388,9 +1388,7 @@ nb_status nb_engine_create(nb_engine **out, size_t arena_bytes, void *cuda_strea
         if (arena_bytes < ((size_t)1 << 20)) return fail(NB_ERR_ARG, "arena must be at least 1 MiB");
         nb_engine *g = new nb_engine();
         g->stream = (cudaStream_t)cuda_stream;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
+        g->sms = device_sms();
         {
             const char *st = getenv("NEKGB_F32_STAGED");
             g->f32_plain = st && st[0] == '0';

@@ -189,9 +189,7 @@ nb_status launch_box_coords(nb_ctx *c, double *xyz) {
     if (st != NB_OK) return st;
     gp.amp = c->box_amp;
     gp.s[0] = c->box_s[0]; gp.s[1] = c->box_s[1]; gp.s[2] = c->box_s[2];
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = device_sms();
     box_coords_kernel<<<grid_blocks(c->m.npts, 256, sms * 8), 256, 0, c->stream>>>(xyz, c->m, gp);
     NB_LAUNCH_CHECK("box_coords_kernel");
     return NB_OK;
@@ -205,9 +203,7 @@ nb_status launch_box_geometry(nb_ctx *c, double amp, const double *s, int *bad_d
     for (int q = 0; q < n * n; q++) gp.D[q] = c->D_host[q];
     gp.amp = amp;
     gp.s[0] = s[0]; gp.s[1] = s[1]; gp.s[2] = s[2];
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = device_sms();
     const int grid = (int)(c->m.E < (int64_t)sms * 8 ? c->m.E : (int64_t)sms * 8);
     box_geometry_kernel<double><<<grid, 256, 0, c->stream>>>(c->d_gxyz, c->m, gp, bad_dev);
     NB_LAUNCH_CHECK("box_geometry_kernel");
@@ -224,9 +220,7 @@ nb_status launch_box_geometry_pairs(const Mesh &m, double amp, const double *s, 
     for (int q = 0; q < m.n * m.n; q++) gp.D[q] = D[q];
     gp.amp = amp;
     gp.s[0] = s[0]; gp.s[1] = s[1]; gp.s[2] = s[2];
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = device_sms();
     const int grid = (int)(m.E < (int64_t)sms * 8 ? m.E : (int64_t)sms * 8);
     box_geometry_kernel<float2><<<grid, 256, 0, stream>>>(out, m, gp, bad_dev);
     NB_LAUNCH_CHECK("box_geometry_kernel<pairs>");

@@ -167,16 +167,7 @@ __global__ void tables_kernel(int64_t *__restrict__ gid, int32_t *__restrict__ m
 }
 
 
-static int sm_count() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms < 1) sms = 1;
-    }
-    return sms;
-}
+static int sm_count() { return device_sms(); }
 
 
 // One wave of CTAs (five per SM, the kernel's register bound) striding over

@@ -38,6 +38,8 @@ cudaError_t dev_alloc(void **p, size_t bytes);
 // Allow `bytes` of dynamic shared memory for a kernel on the current device
 // (set once per kernel and device; thread-safe).
 nb_status smem_attr(const void *kernel, size_t bytes);
+// Number of SMs of the current device (queried once per device; thread-safe).
+int device_sms();
 template <typename K>
 inline nb_status set_smem(K *kernel, size_t bytes) {
     return smem_attr(reinterpret_cast<const void *>(kernel), bytes);

@@ -33,16 +33,7 @@ nb_status launch_assemble_update32(nb_ctx *c);     // assemble.cu
 
 constexpr int kT = 256;
 
-static int sms32() {
-    static int v = 0;
-    if (!v) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        if (v < 1) v = 1;
-    }
-    return v;
-}
+static int sms32() { return device_sms(); }
 
 __global__ void to_f32_kernel(const double *__restrict__ x, float *__restrict__ y, int64_t n) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;

@@ -79,10 +79,7 @@ nb_status set_preconditioner(nb_ctx *c, int kind) {
             if (e != cudaSuccess) return cuda_fail(e, "alloc Jacobi diagonal");
             c->device_bytes += sizeof(double) * c->m.npts;
         }
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int grid = grid_blocks(c->m.npts, 256, sms * 8);
+        const int grid = grid_blocks(c->m.npts, 256, device_sms() * 8);
         diag_e_kernel<<<grid, 256, 0, c->stream>>>(c->d_gxyz, c->d_D, c->m, c->d_minv);
         NB_LAUNCH_CHECK("diag_e_kernel");
         nb_status s = launch_dssum_sc(c, c->d_minv, nullptr);
