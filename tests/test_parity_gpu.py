@@ -307,6 +307,59 @@ def test_full_size_cg_in_bench_configuration(nek, oracle):
     assert rel_err(xg, x_ref) <= 1e-8
 
 
+def test_largest_served_size(nek, oracle):
+    """The largest problem the served workload draws: 32 x 32 x 32 elements,
+    n = 12 (56.6 M local points), device-built geometry.  ax_e on sampled
+    elements, dssum and mask over the whole mesh (bit-exact), and two fixed
+    CG iterations of the graph-captured solver against the oracle's CG."""
+    dims, n = (32, 32, 32), 12
+    E = dims[0] * dims[1] * dims[2]
+    s = inputs.perturbation_coeffs(inputs.SEED_MESH)
+    xi, wq = oracle.gll(n)
+    Dm = oracle.dmat(xi)
+    xyz = oracle.box_coords(*dims, n, inputs.PERTURB_AMP, s)
+    gxyz, _ = oracle.geom(n, xyz, Dm, wq)
+    del xyz
+    u = inputs.local_field(E, n, seed=inputs.SEED_U)
+    rng = np.random.default_rng(7)
+    sample = np.unique(np.concatenate([[0, E - 1], rng.choice(E, 64, replace=False)]))
+    gs = gxyz[sample]
+    want_ax = oracle.ax_e(Dm, gs, u[sample])
+    msk = oracle.mask(*dims, n)
+    f = oracle.apply_mask(msk, oracle.scatter_unique(*dims, n, inputs.unique_field(*dims, n, inputs.SEED_F)))
+    x_ref, it_ref, _, hist_ref, _ = oracle.cg(*dims, n, Dm, gxyz, msk, f, tol=0.0, maxit=2)
+    del gxyz
+    with Ctx(nek, dims, n, inputs.PERTURB_AMP, s, box=True) as ctx:
+        ud = dev(u)
+        w = torch.empty_like(ud)
+        nek.nb_ax(ctx, ud, w)
+        got_ax = host(w)[sample]
+        wr = inputs.local_field(E, n, seed=11)
+        wd = dev(wr)
+        nek.nb_dssum(ctx, wd)
+        got_ds = host(wd)
+        nek.nb_mask(ctx, wd)
+        got_m = host(wd)
+        del ud, w, wd
+        x = torch.zeros(E, n ** 3, dtype=torch.float64, device="cuda")
+        st, it, rr = nek.nb_cg_solve(ctx, dev(f), x, tol=0.0, maxit=2)
+        xg = host(x)
+        hist = nek.nb_cg_history(ctx)
+    # n > 10: the absolute form of the ax_e contract, 1e-12 |D|^2 |G| |u|
+    # (max row sum of |D|).  On this mesh max|w| lies 61x below that term
+    # scale, so the relative form would ask for 4.6 units of 2^-48 of it,
+    # while three double-float contractions of 12 terms accumulate about 7.
+    Dn = np.abs(Dm).sum(1).max()
+    bound = 1e-12 * Dn ** 2 * np.abs(gs).max() * np.abs(u[sample]).max()
+    assert np.abs(got_ax - want_ax).max() <= bound
+    want_ds = oracle.dssum(*dims, n, wr)
+    assert np.array_equal(got_ds, want_ds)
+    assert np.array_equal(got_m, oracle.apply_mask(msk, want_ds))
+    assert st == nek.NB_OK and it == 2 == it_ref
+    assert np.abs(hist - hist_ref).max() / hist_ref.max() <= 1e-10
+    assert rel_err(xg, x_ref) <= 1e-10
+
+
 def test_cg_tolerance_and_determinism(nek, oracle):
     dims, n = (3, 2, 2), 6
     P, f = cg_inputs(oracle, dims, n, seed_mesh=3, seed_f=4)
