@@ -106,10 +106,15 @@ assemble_update_kernel(T *__restrict__ r, const T *__restrict__ w, Mesh m, DsCat
     if (!last_block_reduce<1>(v, partials, 0, blockIdx.x, gridDim.x, gridDim.x, &sc->ticket, tot)) return;
     if (threadIdx.x != 0) return;
     const double rho = tot[0];
+    // <p,p>_c of the next search direction p' = r' + beta p: r' is
+    // orthogonal to p, so <p',p'>_c = rho' + beta^2 <p,p>_c (p_0 = r_0).
+    // Only a scale for the head's pairs is taken from it.
+    const double pprev = sc->it == 0 ? sc->rho : sc->pn2;
     sc->rr = rho;
     sc->rho_old = sc->rho;
     sc->rho = rho;
     sc->beta = rho / sc->rho_old;
+    sc->pn2 = fma(sc->beta * sc->beta, pprev, rho);
     const int it = sc->it + 1;
     sc->it = it;
     if (hist) hist[it] = rho;

@@ -46,6 +46,132 @@ struct AxDfArgs {
     int64_t E;
 };
 
+// The unpreconditioned two-kernel CG head with a software-pipelined element
+// loop.  The pairs of p are scaled by one power of two per iteration,
+// 2^sh with sqrt(<p,p>_c) 2^sh in [1, 2) (<p,p>_c from the scalar block;
+// every |p| is at most sqrt(8 <p,p>_c), as c >= 1/8), instead of a
+// per-element maximum: that removes the exponent reduction and its barrier,
+// and lets p be split straight from registers into shared memory.  Tiny
+// entries lose low-order bits only below 2^-78 of that scale, far under the
+// operator's rounding relative to max|w|.  The six shared arrays rotate
+// roles between consecutive elements (X the input, F the three derivative
+// arrays, P the three partials):
+//   even element: X = S0, F = (S1, S2, S3), P = (S0, S4, S5)
+//   odd element:  X = S1, F = (S0, S2, S3), P = (S1, S4, S5)
+// so the next element is staged into its X while the final pass reads the
+// current P, which needs no barrier in between: four barriers per element.
+template <int N, bool EO>
+__device__ __forceinline__ void cg_head_pipelined(const AxDfArgs &a, double beta, double xa,
+                                                  const typename DfConsts<N, EO>::type &D, float2 *sm,
+                                                  double &dot) {
+    constexpr int N2 = N * N, N3 = N * N * N;
+    constexpr int T = ax_df_threads(N);
+    const int t = threadIdx.x;
+    const double pn = a.sc->it == 0 ? a.sc->rr : a.sc->pn2;
+    const int ep = (int)((__double_as_longlong(pn) >> 52) & 0x7ff);
+    const int sh_in = ep == 0 ? 0 : -((ep - 1023) >> 1);
+    const int sh_out = -sh_in + (a.gexp - 1023);
+    float2 *S0 = sm, *S1 = sm + N3, *S2 = sm + 2 * N3, *S3 = sm + 3 * N3, *S4 = sm + 4 * N3, *S5 = sm + 5 * N3;
+    // x += xa p (the owed update), p = r + beta p, X = pairs of p 2^sh
+    auto stage = [&](int64_t e, float2 *X) {
+        const int64_t eb = e * N3;
+        double *p = a.p + eb;
+        const double *r = a.r + eb;
+        if (xa != 0.0) {
+            double *x = a.x + eb;
+            for (int q = t; q < N3; q += T) {
+                const double pold = p[q];
+                __stcs(x + q, fma(xa, pold, __ldcs(x + q)));
+                const double v = fma(beta, pold, r[q]);
+                p[q] = v;
+                X[q] = dfa::split_scaled<true>(v, sh_in);
+            }
+        } else {
+            for (int q = t; q < N3; q += T) {
+                const double v = fma(beta, p[q], r[q]);
+                p[q] = v;
+                X[q] = dfa::split_scaled<true>(v, sh_in);
+            }
+        }
+    };
+    int64_t e = blockIdx.x;
+    if (e < a.E) stage(e, S0);
+    __syncthreads();
+    for (int k = 0; e < a.E; k++, e += gridDim.x) {
+        const bool odd = k & 1;
+        float2 *X = odd ? S1 : S0;
+        float2 *F0 = odd ? S0 : S1;
+        // forward: wr, ws, wt along this thread's line
+        for (int task = t; task < 3 * N2; task += T) {
+            int stride;
+            const int base = line_of<N>(task, stride);
+            float2 *Fd = task < N2 ? F0 : (task < 2 * N2 ? S2 : S3);
+            if constexpr (EO)
+                line_eo<N>(X, Fd, base, stride, D.fwd);
+            else
+                line_plain<N, false>(X, Fd, base, stride, D);
+        }
+        __syncthreads();
+        // geometric contraction, pointwise, in place
+        const float2 *g = a.g + e * 6 * N3;
+        for (int q = t; q < N3; q += T) {
+            const float2 wr = F0[q], ws = S2[q], wt = S3[q];
+            const float2 g0 = __ldcs(g + q), g1 = __ldcs(g + N3 + q), g2 = __ldcs(g + 2 * N3 + q);
+            const float2 g3 = __ldcs(g + 3 * N3 + q), g4 = __ldcs(g + 4 * N3 + q), g5 = __ldcs(g + 5 * N3 + q);
+            dfa::Acc ur = dfa::first(g0.x, g0.y, wr.x, wr.y);
+            dfa::fma(ur, g1.x, g1.y, ws.x, ws.y);
+            dfa::fma(ur, g2.x, g2.y, wt.x, wt.y);
+            dfa::Acc us = dfa::first(g1.x, g1.y, wr.x, wr.y);
+            dfa::fma(us, g3.x, g3.y, ws.x, ws.y);
+            dfa::fma(us, g4.x, g4.y, wt.x, wt.y);
+            dfa::Acc ut = dfa::first(g2.x, g2.y, wr.x, wr.y);
+            dfa::fma(ut, g4.x, g4.y, ws.x, ws.y);
+            dfa::fma(ut, g5.x, g5.y, wt.x, wt.y);
+            F0[q] = dfa::norm(ur);
+            S2[q] = dfa::norm(us);
+            S3[q] = dfa::norm(ut);
+        }
+        __syncthreads();
+        // backward: the three partials of w, into X (consumed), S4, S5
+        for (int task = t; task < 3 * N2; task += T) {
+            int stride;
+            const int base = line_of<N>(task, stride);
+            const float2 *Fd = task < N2 ? F0 : (task < 2 * N2 ? S2 : S3);
+            float2 *Pd = task < N2 ? X : (task < 2 * N2 ? S4 : S5);
+            if constexpr (EO)
+                line_eo<N>(Fd, Pd, base, stride, D.bwd);
+            else
+                line_plain<N, true>(Fd, Pd, base, stride, D);
+        }
+        __syncthreads();
+        // w = sum of the partials, box faces zeroed, local products w p;
+        // then the next element is staged into the other input array
+        {
+            int ex, ey, ez;
+            element_coords(e, a.m, ex, ey, ez);
+            const unsigned bf = box_faces(ex, ey, ez, a.m);
+            const int64_t eb = e * N3;
+            const double *p = a.p + eb;
+            double *w = a.w + eb;
+#pragma unroll
+            for (int kk = 0; kk < df_points_per_thread<N, T>(); kk++) {
+                const int q = t + kk * T;
+                if (df_points_per_thread<N, T>() * T != N3 && q >= N3) break;
+                const float2 s = dfa::add(dfa::add(X[q], S4[q]), S5[q]);
+                double wv = dfa::join_scaled(s, sh_out);
+                if (point_faces<N>(q) & bf)
+                    wv = 0.0;
+                else
+                    dot = fma(wv, p[q], dot);
+                w[q] = wv;
+            }
+        }
+        const int64_t en = e + gridDim.x;
+        if (en < a.E) stage(en, odd ? S0 : S1);
+        __syncthreads();
+    }
+}
+
 // As many CTAs per SM as the shared memory holds (df_min_blocks); the
 // register bound keeps them resident.
 template <int N, int MODE, bool EO>
@@ -61,6 +187,9 @@ ax_df_kernel(AxDfArgs a, const __grid_constant__ typename DfConsts<N, EO>::type 
         beta = a.sc->it == 0 ? 0.0 : a.sc->beta;
         xa = a.sc->x_alpha;
     }
+    if (MODE == 1 && a.fuse && a.finalize && !a.minv) {
+        cg_head_pipelined<N, EO>(a, beta, xa, D, sm, dot);
+    } else {
     if (threadIdx.x == 0) s_emax = 0;
     __syncthreads();
     for (int64_t e = blockIdx.x; e < a.E; e += gridDim.x) {
@@ -76,6 +205,7 @@ ax_df_kernel(AxDfArgs a, const __grid_constant__ typename DfConsts<N, EO>::type 
         int ex = 0, ey = 0, ez = 0;
         if (MODE == 1) element_coords(e, a.m, ex, ey, ez);
         df_element<N, MODE, EO>(io, beta, xa, a.fuse != 0, a.gexp, a.m, ex, ey, ez, D, sm, &s_emax, dot);
+    }
     }
     if (MODE == 1 && a.fuse) {
         if (a.finalize) {

@@ -85,6 +85,7 @@ struct CgScalars {
     double fnorm2;     // <f,f>_c
     double tol;        // relative tolerance (<= 0: fixed iterations)
     double x_alpha;    // alpha of the x update still owed to x (0: none)
+    double pn2;        // <p,p>_c of the next iteration's p (unpreconditioned CG; see assemble.cu)
     int it;            // iterations completed
     int maxit;
     int done;          // 1: no further iteration runs
