@@ -39,6 +39,7 @@ struct AxDfArgs {
     CgScalars *sc;        // MODE 1
     double *partials;     // MODE 1 fused: one <w,p> partial per CTA
     int finalize;         // MODE 1 fused: the last CTA reduces <w,p>_c and forms alpha
+    double *epart;        // MODE 1 two-kernel CG: one <w,p>_c share per element
     int fuse;             // MODE 1: zero box-face points, local products w p
     Mesh m;
     const float2 *g;      // gxyz pairs [E][6][n^3], scaled by 2^-(gexp-1023)
@@ -46,27 +47,48 @@ struct AxDfArgs {
     int64_t E;
 };
 
-// The unpreconditioned two-kernel CG head with a software-pipelined element
-// loop.  The pairs of p are scaled by one power of two per iteration,
-// 2^sh with sqrt(<p,p>_c) 2^sh in [1, 2) (<p,p>_c from the scalar block;
-// every |p| is at most sqrt(8 <p,p>_c), as c >= 1/8), instead of a
-// per-element maximum: that removes the exponent reduction and its barrier,
-// and lets p be split straight from registers into shared memory.  Tiny
-// entries lose low-order bits only below 2^-78 of that scale, far under the
-// operator's rounding relative to max|w|.  The six shared arrays rotate
-// roles between consecutive elements (X the input, F the three derivative
-// arrays, P the three partials):
-//   even element: X = S0, F = (S1, S2, S3), P = (S0, S4, S5)
-//   odd element:  X = S1, F = (S0, S2, S3), P = (S1, S4, S5)
+// The unpreconditioned two-kernel CG head with a software-pipelined,
+// dynamically scheduled element loop.
+//
+// Scale.  The pairs of p are scaled by one power of two per iteration, 2^sh
+// with sqrt(<p,p>_c) 2^sh in [1, 2) (<p,p>_c from the scalar block; every
+// |p| is at most sqrt(8 <p,p>_c), as c >= 1/8), instead of a per-element
+// maximum: that removes the exponent reduction and its barrier, and lets p
+// be split straight from registers into shared memory.  Tiny entries lose
+// low-order bits only below 2^-78 of that scale, far under the operator's
+// rounding relative to max|w|.
+//
+// Pipeline.  The six shared arrays rotate roles between consecutive
+// elements (X the input, F the three derivative arrays, P the partials):
+//   even step: X = S0, F = (S1, S2, S3), P = (S0, S4, S5)
+//   odd step:  X = S1, F = (S0, S2, S3), P = (S1, S4, S5)
 // so the next element is staged into its X while the final pass reads the
 // current P, which needs no barrier in between: four barriers per element.
+//
+// Schedule.  After its first element (blockIdx.x) a CTA takes the next one
+// from a counter in the scalar block, so SMs that run slower take fewer
+// elements (a static assignment left the slowest SM 12 % behind the mean).
+// <w,p>_c stays independent of the schedule: each element's share is
+// summed in a fixed order into its own slot (each thread's points; the
+// thread sums are added by the last warp, which has a point less to do than
+// the first warps in the pointwise pass: each lane over a fixed set of
+// threads, then a shuffle tree), and the last CTA adds the slots in element
+// order.  A thread keeps its sum in a register until the end of the next
+// element's forward pass before it stores it, so the loads of p and the FP64
+// multiply-adds behind it never hold up a barrier; the last warp adds the
+// sums in that element's pointwise pass.  The counter is read at the start
+// of a step and published just before the barrier that ends the backward
+// pass, which hides the atomic's latency.
 template <int N, bool EO>
 __device__ __forceinline__ void cg_head_pipelined(const AxDfArgs &a, double beta, double xa,
-                                                  const typename DfConsts<N, EO>::type &D, float2 *sm,
-                                                  double &dot) {
+                                                  const typename DfConsts<N, EO>::type &D, float2 *sm) {
     constexpr int N2 = N * N, N3 = N * N * N;
     constexpr int T = ax_df_threads(N);
-    const int t = threadIdx.x;
+    constexpr int NW = T / 32;
+    __shared__ double s_td[T];             // per-thread shares of the previous element
+    __shared__ long long s_next, s_prev;   // s_prev: the element whose shares await the last warp
+    const int t = threadIdx.x, lane = t & 31;
+    const bool last_warp = t >= T - 32;
     const double pn = a.sc->it == 0 ? a.sc->rr : a.sc->pn2;
     const int ep = (int)((__double_as_longlong(pn) >> 52) & 0x7ff);
     const int sh_in = ep == 0 ? 0 : -((ep - 1023) >> 1);
@@ -94,11 +116,24 @@ __device__ __forceinline__ void cg_head_pipelined(const AxDfArgs &a, double beta
             }
         }
     };
+    // the last warp: the share of element s_prev, whose thread sums are in s_td
+    auto flush = [&]() {
+        double v = 0.0;
+#pragma unroll
+        for (int j = 0; j < NW; j++) v += s_td[lane + 32 * j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) a.epart[s_prev] = v;
+    };
     int64_t e = blockIdx.x;
+    if (t == T - 32) s_prev = -1;
     if (e < a.E) stage(e, S0);
     __syncthreads();
-    for (int k = 0; e < a.E; k++, e += gridDim.x) {
+    double de = 0.0;   // this thread's share of the previous element
+    for (int k = 0; e < a.E; k++) {
         const bool odd = k & 1;
+        unsigned nxt = 0;
+        if (t == 0) nxt = atomicAdd(&a.sc->next_elem, 1u);
         float2 *X = odd ? S1 : S0;
         float2 *F0 = odd ? S0 : S1;
         // forward: wr, ws, wt along this thread's line
@@ -111,6 +146,7 @@ __device__ __forceinline__ void cg_head_pipelined(const AxDfArgs &a, double beta
             else
                 line_plain<N, false>(X, Fd, base, stride, D);
         }
+        s_td[t] = de;
         __syncthreads();
         // geometric contraction, pointwise, in place
         const float2 *g = a.g + e * 6 * N3;
@@ -131,6 +167,11 @@ __device__ __forceinline__ void cg_head_pipelined(const AxDfArgs &a, double beta
             S2[q] = dfa::norm(us);
             S3[q] = dfa::norm(ut);
         }
+        if (last_warp) {
+            if (s_prev >= 0) flush();
+            __syncwarp();
+            if (t == T - 32) s_prev = e;
+        }
         __syncthreads();
         // backward: the three partials of w, into X (consumed), S4, S5
         for (int task = t; task < 3 * N2; task += T) {
@@ -143,9 +184,12 @@ __device__ __forceinline__ void cg_head_pipelined(const AxDfArgs &a, double beta
             else
                 line_plain<N, true>(Fd, Pd, base, stride, D);
         }
+        if (t == 0) s_next = (long long)gridDim.x + (long long)nxt;
         __syncthreads();
-        // w = sum of the partials, box faces zeroed, local products w p;
-        // then the next element is staged into the other input array
+        // w = sum of the partials, box faces zeroed, the element's share of
+        // <w,p>_c; then the next element is staged into the other input
+        // array
+        de = 0.0;
         {
             int ex, ey, ez;
             element_coords(e, a.m, ex, ey, ez);
@@ -162,14 +206,18 @@ __device__ __forceinline__ void cg_head_pipelined(const AxDfArgs &a, double beta
                 if (point_faces<N>(q) & bf)
                     wv = 0.0;
                 else
-                    dot = fma(wv, p[q], dot);
+                    de = fma(wv, p[q], de);
                 w[q] = wv;
             }
         }
-        const int64_t en = e + gridDim.x;
+        const int64_t en = s_next;
         if (en < a.E) stage(en, odd ? S0 : S1);
         __syncthreads();
+        e = en;
     }
+    s_td[t] = de;
+    __syncthreads();
+    if (last_warp && s_prev >= 0) flush();
 }
 
 // As many CTAs per SM as the shared memory holds (df_min_blocks); the
@@ -188,7 +236,36 @@ ax_df_kernel(AxDfArgs a, const __grid_constant__ typename DfConsts<N, EO>::type 
         xa = a.sc->x_alpha;
     }
     if (MODE == 1 && a.fuse && a.finalize && !a.minv) {
-        cg_head_pipelined<N, EO>(a, beta, xa, D, sm, dot);
+        // every element's share of <w,p>_c is in epart; the last CTA adds
+        // them in element order and forms alpha
+        cg_head_pipelined<N, EO>(a, beta, xa, D, sm);
+        __shared__ int s_last;
+        if (threadIdx.x == blockDim.x - 32) {   // the thread that wrote this CTA's slots
+            __threadfence();
+            s_last = atomicAdd(&a.sc->ticket, 1u) == gridDim.x - 1;
+        }
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        // eight independent loads per round (a fixed order of additions per thread)
+        double acc = 0.0;
+        const int64_t bs = blockDim.x;
+        int64_t q = threadIdx.x;
+        for (; q + 7 * bs < a.E; q += 8 * bs) {
+            double v[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) v[j] = __ldcg(a.epart + q + j * bs);
+#pragma unroll
+            for (int j = 0; j < 8; j++) acc += v[j];
+        }
+        for (; q < a.E; q += bs) acc += __ldcg(a.epart + q);
+        const double pap = block_sum(acc, red);
+        if (threadIdx.x == 0) {
+            a.sc->ticket = 0;
+            a.sc->next_elem = 0;
+            finalize_alpha(a.sc, pap);
+        }
+        return;
     } else {
     if (threadIdx.x == 0) s_emax = 0;
     __syncthreads();
@@ -305,6 +382,7 @@ static nb_status launch_df_nv(nb_ctx *c, const double *u, double *w, int mode) {
         args.partials = c->d_partials;
         args.fuse = c->fused_cg ? 1 : 0;
         args.finalize = c->two_kernel ? 1 : 0;
+        args.epart = c->d_epart;
     }
     args.m = c->m;
     auto kern = mode == 0 ? ax_df_kernel<N, 0, EO> : ax_df_kernel<N, 1, EO>;

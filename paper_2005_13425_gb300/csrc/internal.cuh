@@ -91,7 +91,7 @@ struct CgScalars {
     int done;          // 1: no further iteration runs
     int status;        // 0 ok, NB_ERR_BREAKDOWN
     unsigned int ticket;  // last-block-done counter for reductions
-    int pad;
+    unsigned int next_elem;  // element counter of the CG head's dynamic schedule (reset by its last CTA)
 };
 
 struct TimingRec {
@@ -122,6 +122,7 @@ struct nb_ctx {
     double *d_r = nullptr, *d_p = nullptr, *d_w = nullptr, *d_x = nullptr;
     double *d_partials = nullptr;
     int partial_cap = 0;
+    double *d_epart = nullptr;          // per-element shares of <w,p>_c (CG head), E entries
     double *d_minv = nullptr;           // Jacobi: 1/diag(A) (0 at Dirichlet points), or null
     nekgb::CgScalars *d_sc = nullptr;
     nekgb::CgScalars *h_sc = nullptr;   // pinned mirror
