@@ -21,7 +21,8 @@
 // (streamed from HBM, coalesced) into (ur, us, ut) in place.  The backward
 // phase is the same line pattern with D^T, each direction writing its own
 // partial array, and a final pointwise phase adds the three partials and
-// writes w.  Four barriers per element; shared memory holds six n^3 arrays
+// writes w.  Six barriers per element (four in the CG head, see
+// cg_head_pipelined); shared memory holds six n^3 arrays
 // of pairs (48 KB at n = 10).
 #include <math.h>
 

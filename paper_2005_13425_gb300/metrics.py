@@ -114,11 +114,21 @@ def measured_peaks(root: str):
 CG_HEAD_SOURCES = ("ax_df.cu", "ax_df_core.cuh", "df.cuh", "reduce.cuh")
 
 
+_C_COMMENT = re.compile(r"//[^\n]*|/\*.*?\*/", re.S)
+
+
+def code_tokens(text: str) -> str:
+    """C/C++ source with comments removed and whitespace collapsed: what
+    the compiler sees, so that editing a comment keeps a digest valid.
+    (String literals holding comment markers do not occur in these files.)"""
+    return " ".join(_C_COMMENT.sub(" ", text).split())
+
+
 def source_digest(csrc_dir: str, names=CG_HEAD_SOURCES) -> str:
     h = hashlib.sha256()
     for nm in names:
-        with open(os.path.join(csrc_dir, nm), "rb") as fh:
-            h.update(nm.encode() + b"\0" + fh.read())
+        with open(os.path.join(csrc_dir, nm), encoding="utf-8") as fh:
+            h.update(nm.encode() + b"\0" + code_tokens(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -58,3 +58,13 @@ def test_recorded_traffic_needs_matching_digest(tmp_path):
     assert metrics.recorded_traffic(str(p), "abcdef0123456789") == 393216000
     assert metrics.recorded_traffic(str(p), "0000000000000000") is None
     assert metrics.recorded_traffic(str(tmp_path / "missing.md"), "abcdef0123456789") is None
+
+
+def test_source_digest_ignores_comments_only(tmp_path):
+    code = "int f(int a) {\n    return a + 1;  // one more\n}\n/* block\n comment */\n"
+    (tmp_path / "k.cu").write_text(code)
+    d0 = metrics.source_digest(str(tmp_path), ("k.cu",))
+    (tmp_path / "k.cu").write_text(code.replace("one more", "the successor").replace("block", "other"))
+    assert metrics.source_digest(str(tmp_path), ("k.cu",)) == d0
+    (tmp_path / "k.cu").write_text(code.replace("a + 1", "a + 2"))
+    assert metrics.source_digest(str(tmp_path), ("k.cu",)) != d0
