@@ -3,7 +3,7 @@
 Each CUDA source compiles in parallel to an object file under ``_build/``;
 the objects link into ``paper_2005_13425_gb300/libnekgb.so``.  Only nvcc and
 the host compiler are needed (no cmake, no torch extension machinery), so
-the same command builds on the x86 development host and on the Arm GPU machine.
+the same command builds on x86-64 and on aarch64 (Grace) hosts.
 """
 from __future__ import annotations
 
