@@ -361,6 +361,27 @@ def test_largest_served_size(nek, oracle):
     assert rel_err(xg, x_ref) <= 1e-10
 
 
+@pytest.mark.parametrize("k", [-90, 80])
+def test_cg_scale_equivariance(nek, oracle, k):
+    """Every step of the FP64-accurate CG commutes with scaling by a power of
+    two: FP64 operations, the pair scales taken from exponents (per element
+    for u, per iteration from <p,p>_c in the CG head) and <r,r>_c on the FP32
+    pipes.  So f 2^k must give x 2^k bit for bit, and the same iteration
+    history scaled by 2^2k."""
+    dims, n = (4, 3, 3), 10
+    P, f = cg_inputs(oracle, dims, n, seed_mesh=5, seed_f=6)
+    out = []
+    with Ctx(nek, dims, n, P["D"], P["gxyz"]) as ctx:
+        for scale in (1.0, 2.0 ** k):
+            x = torch.zeros(P["E"], n ** 3, dtype=torch.float64, device="cuda")
+            st, it, rr = nek.nb_cg_solve(ctx, dev(f * scale), x, tol=0.0, maxit=40)
+            out.append((host(x), nek.nb_cg_history(ctx), st, it))
+    (x0, h0, s0, i0), (x1, h1, s1, i1) = out
+    assert s0 == s1 == nek.NB_OK and i0 == i1 == 40
+    assert np.array_equal(x1, x0 * 2.0 ** k)
+    assert np.array_equal(h1, h0 * 2.0 ** (2 * k))
+
+
 def test_cg_tolerance_and_determinism(nek, oracle):
     dims, n = (3, 2, 2), 6
     P, f = cg_inputs(oracle, dims, n, seed_mesh=3, seed_f=4)
