@@ -118,7 +118,7 @@ static void free_ctx(nb_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     void *ptrs[] = {c->d_D, c->d_gxyz, c->d_mask, c->d_Df, c->d_gxyz_df, c->d_gxyz32, c->d_minv,
-                    c->d_r, c->d_p, c->d_w, c->d_x, c->d_partials, c->d_epart, c->d_sc, c->d_hist,
+                    c->d_r, c->d_p, c->d_w, c->d_x, c->d_partials, c->d_sc, c->d_hist,
                     c->d_r32, c->d_p32, c->d_w32, c->d_z32};
     for (void *p : ptrs)
         if (p) cudaFree(p);

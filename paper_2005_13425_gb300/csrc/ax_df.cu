@@ -40,13 +40,67 @@ struct AxDfArgs {
     CgScalars *sc;        // MODE 1
     double *partials;     // MODE 1 fused: one <w,p> partial per CTA
     int finalize;         // MODE 1 fused: the last CTA reduces <w,p>_c and forms alpha
-    double *epart;        // MODE 1 two-kernel CG: one <w,p>_c share per element
+    int dot_shift0;       // MODE 1 two-kernel CG: scale of the exact <w,p>_c sum (see launch_df_nv)
     int fuse;             // MODE 1: zero box-face points, local products w p
     Mesh m;
     const float2 *g;      // gxyz pairs [E][6][n^3], scaled by 2^-(gexp-1023)
     int gexp;             // biased exponent of max|gxyz|
     int64_t E;
 };
+
+// ---- exact 128-bit fixed-point sums (the CG head's <w,p>_c)
+using u128 = unsigned __int128;
+
+// v 2^S truncated toward zero to an integer, as a two's-complement 128-bit
+// value.  The caller's S keeps |v| 2^S below 2^(126 - ...) (see the head), so
+// the shift never passes 73; values whose scaled magnitude is below 1 give 0.
+__device__ __forceinline__ u128 fixed_of(double v, int S) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex == 0) return 0;
+    const unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);
+    int sh = ex - 1075 + S;
+    u128 mag;
+    if (sh >= 0) {
+        sh = sh > 73 ? 73 : sh;
+        mag = (u128)M << sh;
+    } else {
+        mag = sh > -64 ? (u128)(M >> (-sh)) : (u128)0;
+    }
+    return (b >> 63) ? (u128)0 - mag : mag;
+}
+
+__device__ __forceinline__ u128 shfl_down_u128(u128 v, int o) {
+    const unsigned long long lo = __shfl_down_sync(0xffffffffu, (unsigned long long)v, o);
+    const unsigned long long hi = __shfl_down_sync(0xffffffffu, (unsigned long long)(v >> 64), o);
+    return ((u128)hi << 64) | lo;
+}
+
+// Sum over the CTA (modulo 2^128, i.e. exact for the signed values the head
+// produces); the total is valid in thread 0.  red: 2 * (warps) doubles.
+__device__ __forceinline__ u128 block_sum_u128(u128 v, double *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += shfl_down_u128(v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        red[2 * wid] = __longlong_as_double((long long)(unsigned long long)(v >> 64));
+        red[2 * wid + 1] = __longlong_as_double((long long)(unsigned long long)v);
+    }
+    __syncthreads();
+    u128 t = 0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++)
+            t += ((u128)(unsigned long long)__double_as_longlong(red[2 * k]) << 64) |
+                 (unsigned long long)__double_as_longlong(red[2 * k + 1]);
+    return t;
+}
+
+// x 2^k for any k (two exact power-of-two factors).
+__device__ __forceinline__ double scale2(double x, int k) {
+    const int k1 = k / 2, k2 = k - k1;
+    return x * __longlong_as_double((long long)(k1 + 1023) << 52) * __longlong_as_double((long long)(k2 + 1023) << 52);
+}
 
 // The unpreconditioned two-kernel CG head with a software-pipelined,
 // dynamically scheduled element loop.
@@ -69,27 +123,22 @@ struct AxDfArgs {
 // Schedule.  After its first element (blockIdx.x) a CTA takes the next one
 // from a counter in the scalar block, so SMs that run slower take fewer
 // elements (a static assignment left the slowest SM 12 % behind the mean).
-// <w,p>_c stays independent of the schedule: each element's share is
-// summed in a fixed order into its own slot (each thread's points; the
-// thread sums are added by the last warp, which has a point less to do than
-// the first warps in the pointwise pass: each lane over a fixed set of
-// threads, then a shuffle tree), and the last CTA adds the slots in element
-// order.  A thread keeps its sum in a register until the end of the next
-// element's forward pass before it stores it, so the loads of p and the FP64
-// multiply-adds behind it never hold up a barrier; the last warp adds the
-// sums in that element's pointwise pass.  The counter is read at the start
-// of a step and published just before the barrier that ends the backward
-// pass, which hides the atomic's latency.
+// The counter is read at the start of a step and published just before the
+// barrier that ends the backward pass, which hides the atomic's latency.
+// <w,p>_c stays independent of the schedule because it is summed exactly:
+// each thread's share of an element (its points' products, in a fixed
+// order, in FP64) is converted to a 128-bit integer at the fixed scale 2^S
+// (fixed_of, truncating) and added to the thread's integer sum; integer
+// sums do not depend on the order of the additions.  The caller chooses S
+// from <p,p>_c and a bound on the operator so that no sum can overflow
+// (see launch_df_nv); the result is rounded to FP64 once, at the end.
 template <int N, bool EO>
-__device__ __forceinline__ void cg_head_pipelined(const AxDfArgs &a, double beta, double xa,
+__device__ __forceinline__ u128 cg_head_pipelined(const AxDfArgs &a, double beta, double xa, int S,
                                                   const typename DfConsts<N, EO>::type &D, float2 *sm) {
     constexpr int N2 = N * N, N3 = N * N * N;
     constexpr int T = ax_df_threads(N);
-    constexpr int NW = T / 32;
-    __shared__ double s_td[T];             // per-thread shares of the previous element
-    __shared__ long long s_next, s_prev;   // s_prev: the element whose shares await the last warp
-    const int t = threadIdx.x, lane = t & 31;
-    const bool last_warp = t >= T - 32;
+    __shared__ long long s_next;
+    const int t = threadIdx.x;
     const double pn = a.sc->it == 0 ? a.sc->rr : a.sc->pn2;
     const int ep = (int)((__double_as_longlong(pn) >> 52) & 0x7ff);
     const int sh_in = ep == 0 ? 0 : -((ep - 1023) >> 1);
@@ -117,20 +166,10 @@ __device__ __forceinline__ void cg_head_pipelined(const AxDfArgs &a, double beta
             }
         }
     };
-    // the last warp: the share of element s_prev, whose thread sums are in s_td
-    auto flush = [&]() {
-        double v = 0.0;
-#pragma unroll
-        for (int j = 0; j < NW; j++) v += s_td[lane + 32 * j];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) a.epart[s_prev] = v;
-    };
+    u128 acc = 0;
     int64_t e = blockIdx.x;
-    if (t == T - 32) s_prev = -1;
     if (e < a.E) stage(e, S0);
     __syncthreads();
-    double de = 0.0;   // this thread's share of the previous element
     for (int k = 0; e < a.E; k++) {
         const bool odd = k & 1;
         unsigned nxt = 0;
@@ -147,7 +186,6 @@ __device__ __forceinline__ void cg_head_pipelined(const AxDfArgs &a, double beta
             else
                 line_plain<N, false>(X, Fd, base, stride, D);
         }
-        s_td[t] = de;
         __syncthreads();
         // geometric contraction, pointwise, in place
         const float2 *g = a.g + e * 6 * N3;
@@ -168,11 +206,6 @@ __device__ __forceinline__ void cg_head_pipelined(const AxDfArgs &a, double beta
             S2[q] = dfa::norm(us);
             S3[q] = dfa::norm(ut);
         }
-        if (last_warp) {
-            if (s_prev >= 0) flush();
-            __syncwarp();
-            if (t == T - 32) s_prev = e;
-        }
         __syncthreads();
         // backward: the three partials of w, into X (consumed), S4, S5
         for (int task = t; task < 3 * N2; task += T) {
@@ -187,10 +220,9 @@ __device__ __forceinline__ void cg_head_pipelined(const AxDfArgs &a, double beta
         }
         if (t == 0) s_next = (long long)gridDim.x + (long long)nxt;
         __syncthreads();
-        // w = sum of the partials, box faces zeroed, the element's share of
-        // <w,p>_c; then the next element is staged into the other input
-        // array
-        de = 0.0;
+        // w = sum of the partials, box faces zeroed, this thread's share of
+        // <w,p>_c into its exact sum; then the next element is staged into
+        // the other input array
         {
             int ex, ey, ez;
             element_coords(e, a.m, ex, ey, ez);
@@ -198,6 +230,7 @@ __device__ __forceinline__ void cg_head_pipelined(const AxDfArgs &a, double beta
             const int64_t eb = e * N3;
             const double *p = a.p + eb;
             double *w = a.w + eb;
+            double de = 0.0;
 #pragma unroll
             for (int kk = 0; kk < df_points_per_thread<N, T>(); kk++) {
                 const int q = t + kk * T;
@@ -210,15 +243,14 @@ __device__ __forceinline__ void cg_head_pipelined(const AxDfArgs &a, double beta
                     de = fma(wv, p[q], de);
                 w[q] = wv;
             }
+            acc += fixed_of(de, S);
         }
         const int64_t en = s_next;
         if (en < a.E) stage(en, odd ? S0 : S1);
         __syncthreads();
         e = en;
     }
-    s_td[t] = de;
-    __syncthreads();
-    if (last_warp && s_prev >= 0) flush();
+    return acc;
 }
 
 // As many CTAs per SM as the shared memory holds (df_min_blocks); the
@@ -237,31 +269,30 @@ ax_df_kernel(AxDfArgs a, const __grid_constant__ typename DfConsts<N, EO>::type 
         xa = a.sc->x_alpha;
     }
     if (MODE == 1 && a.fuse && a.finalize && !a.minv) {
-        // every element's share of <w,p>_c is in epart; the last CTA adds
-        // them in element order and forms alpha
-        cg_head_pipelined<N, EO>(a, beta, xa, D, sm);
+        // the exact sums: per CTA, then over the CTAs by the last one
+        const double pn = a.sc->it == 0 ? a.sc->rr : a.sc->pn2;
+        const int S = a.dot_shift0 - ((int)((__double_as_longlong(pn) >> 52) & 0x7ff) - 1023);
+        const u128 mine = block_sum_u128(cg_head_pipelined<N, EO>(a, beta, xa, S, D, sm), red);
         __shared__ int s_last;
-        if (threadIdx.x == blockDim.x - 32) {   // the thread that wrote this CTA's slots
+        if (threadIdx.x == 0) {
+            a.partials[2 * blockIdx.x] = __longlong_as_double((long long)(unsigned long long)(mine >> 64));
+            a.partials[2 * blockIdx.x + 1] = __longlong_as_double((long long)(unsigned long long)mine);
             __threadfence();
             s_last = atomicAdd(&a.sc->ticket, 1u) == gridDim.x - 1;
         }
         __syncthreads();
         if (!s_last) return;
         __threadfence();
-        // eight independent loads per round (a fixed order of additions per thread)
-        double acc = 0.0;
-        const int64_t bs = blockDim.x;
-        int64_t q = threadIdx.x;
-        for (; q + 7 * bs < a.E; q += 8 * bs) {
-            double v[8];
-#pragma unroll
-            for (int j = 0; j < 8; j++) v[j] = __ldcg(a.epart + q + j * bs);
-#pragma unroll
-            for (int j = 0; j < 8; j++) acc += v[j];
-        }
-        for (; q < a.E; q += bs) acc += __ldcg(a.epart + q);
-        const double pap = block_sum(acc, red);
+        u128 v = 0;
+        for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x)
+            v += ((u128)(unsigned long long)__double_as_longlong(__ldcg(a.partials + 2 * q)) << 64) |
+                 (unsigned long long)__double_as_longlong(__ldcg(a.partials + 2 * q + 1));
+        v = block_sum_u128(v, red);
         if (threadIdx.x == 0) {
+            // the signed 128-bit total, rounded to FP64 once, scaled back by 2^-S
+            const long long hi = (long long)(unsigned long long)(v >> 64);
+            const unsigned long long lo = (unsigned long long)v;
+            const double pap = scale2(fma((double)hi, 18446744073709551616.0, (double)lo), -S);
             a.sc->ticket = 0;
             a.sc->next_elem = 0;
             finalize_alpha(a.sc, pap);
@@ -357,6 +388,35 @@ bool centro_antisymmetric(const double *D, int n) {
     return asym <= 1e-14 * mx;
 }
 
+// The fixed-point scale of the CG head's exact <w,p>_c: S = dot_shift0 -
+// e(<p,p>_c), e the binary exponent.  Every |w_q| is at most
+// A max|p| with A = 9 |D|_1 |D|_inf max|G| (three derivatives, the 3x3
+// contraction, three transposed derivatives), and max|p| <= sqrt(8 <p,p>_c),
+// so a thread's share of an element (P points) is below
+// 72 P A <p,p>_c < 2^(sa + e) with sa as below (16x margin for the
+// recursion's <p,p>_c).  Summing E T shares (E elements, T threads) then
+// stays below 2^(sa + e + S + log2(E T)) <= 2^125: no 128-bit sum overflows.
+// The grid of the sum, 2^-S, is 2^-(125 - log2(E T)) of that bound.
+template <int N>
+static int dot_shift0(const nb_ctx *c) {
+    constexpr int T = ax_df_threads(N);
+    constexpr int P = (N * N * N + T - 1) / T;
+    double d1 = 0.0, dinf = 0.0;
+    for (int i = 0; i < N; i++) {
+        double rs = 0.0, cs = 0.0;
+        for (int l = 0; l < N; l++) {
+            rs += fabs(c->D_host[i * N + l]);
+            cs += fabs(c->D_host[l * N + i]);
+        }
+        dinf = fmax(dinf, rs);
+        d1 = fmax(d1, cs);
+    }
+    // max|G| < 2^(gexp - 1022)
+    const int sa = (int)ceil(log2(72.0 * P * 9.0 * d1 * dinf)) + (c->gxyz_exp - 1022) + 1 + 4;
+    const int sE = (int)ceil(log2((double)c->m.E * T));
+    return 125 - sE - sa;
+}
+
 template <int N, bool EO>
 static nb_status launch_df_nv(nb_ctx *c, const double *u, double *w, int mode) {
     constexpr int T = ax_df_threads(N);
@@ -383,7 +443,7 @@ static nb_status launch_df_nv(nb_ctx *c, const double *u, double *w, int mode) {
         args.partials = c->d_partials;
         args.fuse = c->fused_cg ? 1 : 0;
         args.finalize = c->two_kernel ? 1 : 0;
-        args.epart = c->d_epart;
+        args.dot_shift0 = dot_shift0<N>(c);
     }
     args.m = c->m;
     auto kern = mode == 0 ? ax_df_kernel<N, 0, EO> : ax_df_kernel<N, 1, EO>;

@@ -304,9 +304,7 @@ nb_status ensure_cg_workspace(nb_ctx *c) {
     c->partial_cap = 2 * (2 * kMaxRedGrid) + 16;
     if ((e = dev_alloc((void **)&c->d_partials, sizeof(double) * c->partial_cap)) != cudaSuccess)
         return cuda_fail(e, "alloc partials");
-    if ((e = dev_alloc((void **)&c->d_epart, sizeof(double) * c->m.E)) != cudaSuccess)
-        return cuda_fail(e, "alloc element partials");
-    c->device_bytes += sizeof(double) * (c->partial_cap + c->m.E);
+    c->device_bytes += sizeof(double) * c->partial_cap;
     if ((e = dev_alloc((void **)&c->d_sc, sizeof(CgScalars))) != cudaSuccess)
         return cuda_fail(e, "alloc scalars");
     if ((e = cudaMallocHost((void **)&c->h_sc, sizeof(CgScalars))) != cudaSuccess)

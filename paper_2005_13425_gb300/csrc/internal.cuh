@@ -122,7 +122,6 @@ struct nb_ctx {
     double *d_r = nullptr, *d_p = nullptr, *d_w = nullptr, *d_x = nullptr;
     double *d_partials = nullptr;
     int partial_cap = 0;
-    double *d_epart = nullptr;          // per-element shares of <w,p>_c (CG head), E entries
     double *d_minv = nullptr;           // Jacobi: 1/diag(A) (0 at Dirichlet points), or null
     nekgb::CgScalars *d_sc = nullptr;
     nekgb::CgScalars *h_sc = nullptr;   // pinned mirror
