@@ -392,9 +392,9 @@ bool centro_antisymmetric(const double *D, int n) {
 // e(<p,p>_c), e the binary exponent.  Every |w_q| is at most
 // A max|p| with A = 9 |D|_1 |D|_inf max|G| (three derivatives, the 3x3
 // contraction, three transposed derivatives), and max|p| <= sqrt(8 <p,p>_c),
-// so a thread's share of an element (P points) is below
-// 72 P A <p,p>_c < 2^(sa + e) with sa as below (16x margin for the
-// recursion's <p,p>_c).  Summing E T shares (E elements, T threads) then
+// so a thread's share of an element (P points) is below 8 P A <p,p>_c.
+// sa below takes 72 P A (a further factor 9 of margin) and another 16x for
+// the recursion's <p,p>_c, so the share stays below 2^(sa + e).  Summing E T shares (E elements, T threads) then
 // stays below 2^(sa + e + S + log2(E T)) <= 2^125: no 128-bit sum overflows.
 // The grid of the sum, 2^-S, is 2^-(125 - log2(E T)) of that bound.
 template <int N>
