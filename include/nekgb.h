@@ -151,7 +151,10 @@ nb_status nb_apply(nb_ctx *ctx, const double *u_dev, double *w_dev);
  * receive the iterations done and sqrt(<r,r>_c/<f,f>_c).  Blocks until the
  * solve is finished.  Returns NB_ERR_NOT_CONVERGED if tol > 0 was not
  * reached within maxit, NB_ERR_BREAKDOWN if <w,p>_c <= 0 or not finite
- * (x then holds the last good iterate).  For NB_MIXED contexts this runs
+ * (x then holds the last good iterate).  Results are bit-for-bit
+ * reproducible: every reduction has a fixed order or is exact (the FP64
+ * head's <w,p>_c is an exact fixed-point sum, so its dynamic element
+ * schedule does not change it).  For NB_MIXED contexts this runs
  * FP64 defect correction around an FP32 inner CG (nb_set_mixed_params):
  * maxit bounds the total inner iterations, *iters_out receives them, and
  * relres is the FP64 residual sqrt(<r,r>_c/<f,f>_c) of the returned x; the
