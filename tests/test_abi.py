@@ -94,3 +94,24 @@ def test_injected_allocation_failure_is_reported():
     assert r.returncode == 0, r.stderr
     st, ctxv, msg = r.stdout.strip().split(" ", 2)
     assert int(st) == 3 and ctxv == "None" and "alloc" in msg
+
+
+def test_engine_footprint_host_arithmetic(nek):
+    """Admission footprint (host-only): gxyz pairs and four FP64 CG vectors
+    (80 B per local point) for FP64 requests; FP64 and FP32 gxyz, three FP64
+    and four FP32 vectors (112 B per point) for mixed ones; plus the tile
+    partials, a small remainder.  Bad arguments are rejected."""
+    for dims, n in [((16, 16, 16), 10), ((4, 4, 4), 8), ((8, 4, 2), 6), ((1, 1, 1), 2)]:
+        E = dims[0] * dims[1] * dims[2]
+        npts = E * n ** 3
+        f64 = nek.nb_engine_footprint(dims, n, nek.NB_FP64)
+        mix = nek.nb_engine_footprint(dims, n, nek.NB_MIXED)
+        assert 80 * npts <= f64 <= 80 * npts + 16 * E + 4096
+        assert 112 * npts <= mix <= 112 * npts + 16 * E + 4096
+    small = nek.nb_engine_footprint((8, 8, 8), 10, nek.NB_FP64)
+    assert nek.nb_engine_footprint((16, 8, 8), 10, nek.NB_FP64) > small
+    for bad in [((0, 1, 1), 10, nek.NB_FP64), ((2, 2, 2), 1, nek.NB_FP64), ((2, 2, 2), 17, nek.NB_FP64),
+                ((2, 2, 2), 8, 7)]:
+        with pytest.raises(nek.NekgbError) as ei:
+            nek.nb_engine_footprint(*bad)
+        assert ei.value.status == nek.NB_ERR_ARG
