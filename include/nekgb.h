@@ -181,18 +181,22 @@ nb_status nb_cg_history(nb_ctx *ctx, double *rho_host, int cap, int *count);
 nb_status nb_dot_c(nb_ctx *ctx, const double *a_dev, const double *b_dev,
                    double *out_host);
 
-/* Allocation-free weighted dot product (the paper has no counterpart; this
- * exists for callers that cannot call cudaMalloc: code recording a CUDA
- * graph, code whose device memory is owned by another allocator, code that
- * must not block).  *out_dev (device, 1 double) = <a,b>_c on the box `mesh`
- * with n points per direction, as nb_dot_c computes it, without a context
- * and without allocating: its scratch is a fixed device array in the
- * library (one partial per element, at most 32768 elements; larger meshes
- * return NB_ERR_ARG).  Asynchronous on cuda_stream.  The first call on a
- * device looks up the array's address (cudaGetSymbolAddress), so make it
- * before any stream capture.  All calls share the one array: calls that
- * overlap on the GPU (different streams, or graphs replayed concurrently)
- * race and give wrong results. */
+/* Allocation-free weighted dot product (the paper has no counterpart).  It
+ * exists for callers that cannot call cudaMalloc: code whose device memory
+ * is all owned by another allocator or a fixed pool (a framework's caching
+ * allocator, an application that reserves the GPU's memory up front), and
+ * code on a latency path that must not block (cudaMalloc and cudaFree can
+ * synchronise the device).  *out_dev (device, 1 double) = <a,b>_c on the
+ * box `mesh` with n points per direction, as nb_dot_c computes it, without
+ * a context and without allocating: its scratch is a fixed device array in
+ * the library (one partial per element, at most 32768 elements; larger
+ * meshes return NB_ERR_ARG before any work).  Asynchronous on cuda_stream.
+ * The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  All calls share the one array, which keeps the last call's
+ * contents (the reduction ticket is cleared on every call): calls that
+ * overlap on the GPU (for example on two streams) race and give wrong
+ * results. */
 nb_status nb_dot_c_noalloc(nb_box mesh, int n, const double *a_dev,
                            const double *b_dev, double *out_dev,
                            void *cuda_stream);

@@ -445,10 +445,10 @@ nb_status cg_solve_fp64(nb_ctx *c, const double *f, double *x, double tol, int m
 }
 
 // ---------------------------------------------------------------- allocation-free dot
-// Some callers cannot call cudaMalloc: code recording a CUDA graph (device
-// allocation is not a capturable stream operation), code running under a
-// memory manager that already owns the device memory, and code that must
-// not block (cudaMalloc may synchronise the device).  For them the weighted
+// Some callers cannot call cudaMalloc: code running under a memory manager
+// that already owns the device memory (a framework's caching allocator, an
+// application that reserves the GPU up front), and code that must not block
+// (cudaMalloc and cudaFree may synchronise the device).  For them the weighted
 // dot product runs the same reduction kernel with its scratch -- one
 // partial sum per element plus the last-CTA ticket -- in a file-scope
 // device array instead of a context's allocation.  Every GPU that loads the

@@ -1258,7 +1258,10 @@ nb_status engine_submit_internal(nb_engine *g, nb_box box, int n, double amp, co
     }
     int *d_bad = (int *)(P.partials);   // scratch: the partials are rewritten before they are read
     double *rhs = mixed ? P.f : P.r;
-    NB_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), g->stream));
+    if ((e = cudaMemsetAsync(d_bad, 0, sizeof(int), g->stream)) != cudaSuccess) {
+        g->arena.release(off, bytes);
+        return cuda_fail(e, "engine: clear geometry flag");
+    }
     s = launch_box_geometry_pairs(m, amp, s3, G.D, P.g, d_bad, g->stream);
     if (s == NB_OK && !f_unique &&
         (e = cudaMemcpyAsync(rhs, f, sizeof(double) * m.npts, cudaMemcpyDeviceToDevice, g->stream)) != cudaSuccess)

@@ -1,8 +1,13 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle.
 
 Tolerances (derived from the arithmetic):
-* ax_e, apply, geometry: max-norm relative error <= 1e-12 (FP64 contract);
-  at n > 10 on the full-size mesh the absolute form 1e-12 |D|^2 |G| |u|.
+* ax_e, apply: max-norm relative error <= 1e-12 (FP64 contract) on identical
+  inputs (the same D and gxyz on both sides), at every n; the absolute form
+  1e-12 |D|^2 |G| |u| only for the near-null input A 1.
+* device-built geometry against the oracle's: n eps kappa_J of max|G|, with
+  kappa_J = |D|_inf max|x| / min|dx/dr| the condition number of the
+  isoparametric Jacobian J = D x (absolute coordinates: two FP64
+  constructions of J differ by about eps kappa_J relative).
 * dssum, mask, numbering, multiplicity, scatter: exact (value equality).
 * weighted dots: relative 1e-13 (reduction order differs).
 * CG: rho history and final x relative <= 1e-8 after 100 fixed iterations
@@ -43,6 +48,15 @@ def host(t):
 
 def rel_err(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def geometry_tol(D, dims, n, amp=0.05):
+    """n eps kappa_J: the rounding bound of the isoparametric Jacobian
+    J = D x on absolute coordinates (|x| <= 1 + amp), relative to its
+    smallest diagonal entry (1/(2 max(dims)) less the perturbation's
+    gradient, at most 3 pi amp of it)."""
+    kappa = np.abs(D).sum(1).max() * (1.0 + amp) / (0.5 / max(dims) * (1.0 - 3.0 * np.pi * amp))
+    return n * np.finfo(np.float64).eps * kappa
 
 
 class Ctx:
@@ -311,8 +325,11 @@ def test_full_size_cg_in_bench_configuration(nek, oracle):
 def test_largest_served_size(nek, oracle):
     """The largest problem the served workload draws: 32 x 32 x 32 elements,
     n = 12 (56.6 M local points), device-built geometry.  ax_e on sampled
-    elements, dssum and mask over the whole mesh (bit-exact), and two fixed
-    CG iterations of the graph-captured solver against the oracle's CG."""
+    elements against the oracle applied to the device's own D and gxyz
+    (identical inputs, the 1e-12 relative contract), the device geometry
+    against the oracle's (n eps kappa_J), dssum and mask over the whole mesh
+    (bit-exact), and two fixed CG iterations of the graph-captured solver
+    against the oracle's CG."""
     dims, n = (32, 32, 32), 12
     E = dims[0] * dims[1] * dims[2]
     s = inputs.perturbation_coeffs(inputs.SEED_MESH)
@@ -325,12 +342,16 @@ def test_largest_served_size(nek, oracle):
     rng = np.random.default_rng(7)
     sample = np.unique(np.concatenate([[0, E - 1], rng.choice(E, 64, replace=False)]))
     gs = gxyz[sample]
-    want_ax = oracle.ax_e(Dm, gs, u[sample])
     msk = oracle.mask(*dims, n)
     f = oracle.apply_mask(msk, oracle.scatter_unique(*dims, n, inputs.unique_field(*dims, n, inputs.SEED_F)))
     x_ref, it_ref, _, hist_ref, _ = oracle.cg(*dims, n, Dm, gxyz, msk, f, tol=0.0, maxit=2)
     del gxyz
     with Ctx(nek, dims, n, inputs.PERTURB_AMP, s, box=True) as ctx:
+        Dd = nek.nb_get_operator(ctx, n)
+        g = torch.empty(E, 6, n ** 3, dtype=torch.float64, device="cuda")
+        nek.nb_get_operator(ctx, n, g)
+        gd = host(g[torch.from_numpy(sample).cuda()])
+        del g
         ud = dev(u)
         w = torch.empty_like(ud)
         nek.nb_ax(ctx, ud, w)
@@ -346,19 +367,41 @@ def test_largest_served_size(nek, oracle):
         st, it, rr = nek.nb_cg_solve(ctx, dev(f), x, tol=0.0, maxit=2)
         xg = host(x)
         hist = nek.nb_cg_history(ctx)
-    # n > 10: the absolute form of the ax_e contract, 1e-12 |D|^2 |G| |u|
-    # (max row sum of |D|).  On this mesh max|w| lies 61x below that term
-    # scale, so the relative form would ask for 4.6 units of 2^-48 of it,
-    # while three double-float contractions of 12 terms accumulate about 7.
-    Dn = np.abs(Dm).sum(1).max()
-    bound = 1e-12 * Dn ** 2 * np.abs(gs).max() * np.abs(u[sample]).max()
-    assert np.abs(got_ax - want_ax).max() <= bound
+    assert rel_err(got_ax, oracle.ax_e(Dd, gd, u[sample])) <= AX_TOL
+    assert rel_err(Dd, Dm) <= 1e-13
+    assert np.abs(gd - gs).max() <= geometry_tol(Dm, dims, n) * np.abs(gs).max()
     want_ds = oracle.dssum(*dims, n, wr)
     assert np.array_equal(got_ds, want_ds)
     assert np.array_equal(got_m, oracle.apply_mask(msk, want_ds))
     assert st == nek.NB_OK and it == 2 == it_ref
     assert np.abs(hist - hist_ref).max() / hist_ref.max() <= 1e-10
     assert rel_err(xg, x_ref) <= 1e-10
+
+
+@pytest.mark.parametrize("dims,n", [((32, 32, 32), 12), ((16, 16, 16), 16)])
+def test_ax_full_size_identical_inputs(nek, oracle, dims, n):
+    """The 1e-12 relative contract at the largest served degree (n = 12 on
+    32^3 elements) and at the largest supported one (n = 16 on 16^3), with
+    the oracle's own D and gxyz handed to nb_setup, checked on sampled
+    elements of the whole-mesh launch."""
+    E = dims[0] * dims[1] * dims[2]
+    s = inputs.perturbation_coeffs(inputs.SEED_MESH)
+    xi, wq = oracle.gll(n)
+    Dm = oracle.dmat(xi)
+    xyz = oracle.box_coords(*dims, n, inputs.PERTURB_AMP, s)
+    gxyz, _ = oracle.geom(n, xyz, Dm, wq)
+    del xyz
+    u = inputs.local_field(E, n, seed=inputs.SEED_U + n)
+    rng = np.random.default_rng(n)
+    sample = np.unique(np.concatenate([[0, E - 1], rng.choice(E, 64, replace=False)]))
+    want = oracle.ax_e(Dm, gxyz[sample], u[sample])
+    with Ctx(nek, dims, n, Dm, gxyz) as ctx:
+        del gxyz
+        ud = dev(u)
+        w = torch.empty_like(ud)
+        nek.nb_ax(ctx, ud, w)
+        got = host(w[torch.from_numpy(sample).cuda()])
+    assert rel_err(got, want) <= AX_TOL
 
 
 @pytest.mark.parametrize("k", [-90, 80])

@@ -1,13 +1,13 @@
 """The allocation-free weighted dot product, nb_dot_c_noalloc.
 
-Some callers cannot allocate device memory: code that is recording a CUDA
-graph (cudaMalloc is not a capturable stream operation), code whose device
-memory is owned by another allocator, and code that must not block (a
-device allocation can synchronise the device).  nb_dot_c_noalloc serves
-them: it needs no context and keeps its scratch in a fixed device array of
-the library.  This test calls it through the C ABI twice in a row, on
-different inputs, and checks each result against the context-based
-nb_dot_c, with the relative tolerance the other dot-product tests use.
+Some callers cannot allocate device memory: code whose device memory is all
+owned by another allocator or a fixed pool, and code that must not block (a
+device allocation or free can synchronise the device).  nb_dot_c_noalloc
+serves them: it needs no context and keeps its scratch in a fixed device
+array of the library.  This test calls it through the C ABI twice in a row,
+on different inputs, and checks each result against the context-based
+nb_dot_c and against the CPU oracle's dot_c on the same fields, with the
+relative tolerance the other dot-product tests use.
 """
 import numpy as np
 import pytest
@@ -32,21 +32,25 @@ def nek():
 
 
 @pytest.mark.parametrize("dims,n", [((4, 3, 3), 8), ((16, 16, 16), 10)])
-def test_noalloc_dot_matches_context_dot_twice(nek, dims, n):
+def test_noalloc_dot_matches_context_dot_twice(nek, oracle, dims, n):
     stream = torch.cuda.Stream()
     E = dims[0] * dims[1] * dims[2]
+    ah = inputs.local_field(E, n, seed=11)
+    bh = inputs.local_field(E, n, seed=12)
     with torch.cuda.stream(stream):
-        a = torch.from_numpy(inputs.local_field(E, n, seed=11)).cuda()
-        b = torch.from_numpy(inputs.local_field(E, n, seed=12)).cuda()
+        a = torch.from_numpy(ah).cuda()
+        b = torch.from_numpy(bh).cuda()
         out = torch.full((1,), np.nan, dtype=torch.float64, device="cuda")
         ctx = nek.nb_setup_box(dims, n, 0.05, inputs.perturbation_coeffs(0), stream=stream)
         try:
-            for x, y in ((a, b), (b, b)):            # two calls in a row
+            for (x, y), (xh, yh) in zip(((a, b), (b, b)), ((ah, bh), (bh, bh))):   # two calls in a row
                 nek.nb_dot_c_noalloc(dims, n, x, y, out, stream)
                 stream.synchronize()
                 got = float(out.cpu()[0])
                 want = nek.nb_dot_c(ctx, x, y)
                 assert abs(got - want) <= DOT_TOL * abs(want), (got, want)
+                ref = oracle.dot_c(*dims, n, xh, yh)
+                assert abs(got - ref) <= DOT_TOL * abs(ref), (got, ref)
         finally:
             nek.nb_destroy(ctx)
 
