@@ -187,17 +187,65 @@ def time_oracle_cg(iters: int):
     return dt, it
 
 
+class omp_threads:
+    """Run the oracle's OpenMP loops on `k` threads inside the block (the
+    oracle library shares the process's OpenMP runtime)."""
+
+    def __init__(self, k: int):
+        self.k = k
+
+    def __enter__(self):
+        import ctypes
+        self.lib = ctypes.CDLL("libgomp.so.1")
+        self.old = self.lib.omp_get_max_threads()
+        self.lib.omp_set_num_threads(self.k)
+        return self
+
+    def __exit__(self, *a):
+        self.lib.omp_set_num_threads(self.old)
+
+
+def config1_oracle():
+    """Config 1 (4x4x4 elements, n = 8, 100 fixed CG iterations) with the
+    oracle, at all host cores and at one thread (median of 3)."""
+    import oracle
+    dims, n = (4, 4, 4), 8
+    s = inputs.perturbation_coeffs(inputs.SEED_MESH)
+    P = oracle.box_problem(*dims, n, inputs.PERTURB_AMP, s)
+    f = oracle.apply_mask(P["mask"], oracle.scatter_unique(*dims, n, inputs.unique_field(*dims, n, inputs.SEED_F)))
+
+    def run():
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            oracle.cg(*dims, n, P["D"], P["gxyz"], P["mask"], f, tol=0.0, maxit=100)
+            ts.append(time.perf_counter() - t0)
+        return statistics.median(ts)
+    t_all = run()
+    with omp_threads(1):
+        t_one = run()
+    dofs = 64 * n ** 3
+    return {"ms_all_cores": 1e3 * t_all, "ms_one_thread": 1e3 * t_one,
+            "gdofs_all_cores": dofs * 100 / t_all / 1e9, "gdofs_one_thread": dofs * 100 / t_one / 1e9}
+
+
 def cpu_baseline(target_s: float = 15.0):
     """The oracle's CG on the host cores, on a bounded sample of the same
-    workload: a 4-iteration probe sizes the sample to ~target_s seconds."""
+    workload: a 4-iteration probe sizes the sample to ~target_s seconds.
+    Also: the same at one thread (a shorter sample) and config 1."""
     dt0, it0 = time_oracle_cg(4)
     iters = int(max(4, min(2000, target_s / max(dt0 / max(it0, 1), 1e-6))))
     dt, it = time_oracle_cg(iters)
     dofs = P_dofs()
+    with omp_threads(1):
+        dt1, it1 = time_oracle_cg(4)
     return {"value": dofs * it / dt / 1e9, "unit": "GDOF/s", "cores": hardware_threads(),
             "kind": "oracle", "cpu": cpu_model(),
             "sample": f"{it} fixed CG iterations (plus the initial residual) of the same "
-                      f"E=4096, n=10 problem, wall {dt:.2f} s"}
+                      f"E=4096, n=10 problem, wall {dt:.2f} s",
+            "one_thread": {"value": dofs * it1 / dt1 / 1e9, "unit": "GDOF/s", "cores": 1,
+                           "sample": f"{it1} CG iterations of the same problem, wall {dt1:.2f} s"},
+            "config1_4x4x4_n8_cg100": config1_oracle()}
 
 
 def P_dofs() -> int:
@@ -247,7 +295,11 @@ def mixed_vs_fp64(nekgb, stream, n, tol=1e-10):
     import torch
     E = DIMS[0] * DIMS[1] * DIMS[2]
     s = inputs.perturbation_coeffs(inputs.SEED_MESH)
-    out = {"n": n, "E": E, "tol": tol}
+    out = {"n": n, "E": E, "tol": tol,
+           "inputs": "u* at the device-built nodes, f = A u* with the library's FP64 operator "
+                     "(parity-checked against the oracle at 1e-12); the oracle-built f and the "
+                     "comparison with the oracle's FP64 CG solution at this size are the GPU test "
+                     "test_mixed_gpu.py::test_config3_full_size_against_oracle"}
     c64 = nekgb.nb_setup_box(DIMS, n, inputs.PERTURB_AMP, s, nekgb.NB_FP64, stream)
     cmx = nekgb.nb_setup_box(DIMS, n, inputs.PERTURB_AMP, s, nekgb.NB_MIXED, stream)
     try:
@@ -432,7 +484,33 @@ def run_gpu(args, rank, world, local):
         finally:
             nekgb.nb_destroy(cs)
 
+    # ---- config 1: 4x4x4 elements, n = 8, 100 fixed CG iterations (the
+    # paper's run length), median of 20 solves
+    c1 = nekgb.nb_setup_box((4, 4, 4), 8, inputs.PERTURB_AMP, s, nekgb.NB_FP64, stream)
+    try:
+        f1u = torch.from_numpy(inputs.unique_field(4, 4, 4, 8, inputs.SEED_F)).cuda()
+        f1 = torch.empty(64, 8 ** 3, dtype=torch.float64, device="cuda")
+        nekgb.nb_scatter_unique(c1, f1u, f1)
+        nekgb.nb_mask(c1, f1)
+        x1 = torch.zeros_like(f1)
+        t1 = []
+        for rep in range(23):
+            x1.zero_()
+            c0, c1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            nekgb.nb_cg_solve(c1, f1, x1, tol=0.0, maxit=100)
+            c1e.record(stream)
+            c1e.synchronize()
+            if rep >= 3:
+                t1.append(c0.elapsed_time(c1e))
+        config1 = {"mesh": "4x4x4", "n": 8, "cg_iterations": 100, "ms": statistics.median(t1),
+                   "gdofs": 64 * 8 ** 3 * 100 / (statistics.median(t1) * 1e-3) / 1e9,
+                   "note": "32,768 local points: launch- and latency-bound (2 kernels per iteration)"}
+    finally:
+        nekgb.nb_destroy(c1)
+
     # ---- roofline of the dominant kernel, from the timed region's events
+    fp32_peak = nekgb.nb_fp32_rate() / 1e12
     hbm, _, peak_src = metrics.measured_peaks(ROOT)
     ax = kern["ax_e"]
     ax_avg_ms = ax["ms_total"] / max(ax["launches"], 1)
@@ -445,7 +523,7 @@ def run_gpu(args, rank, world, local):
     traffic = None
     if double_float:
         traffic = metrics.recorded_traffic(
-            os.path.join(ROOT, "profiles", "cg_head_ax_df_e4096_n10_traffic.md"),
+            os.path.join(ROOT, "profiles", "traffic.json"), "cg_head_ax_df_e4096_n10",
             metrics.source_digest(os.path.join(ROOT, "paper_2005_13425_gb300", "csrc")))
     roof_hbm = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm, "unit": "GB/s",
                 "frac": hbm_frac, "traffic": traffic,
@@ -457,9 +535,10 @@ def run_gpu(args, rank, world, local):
         # FP32 instruction rate, its work the algorithm's FP32 instructions
         ops = metrics.df_fp32_ops_per_point(NGLL) * D
         ach = ops / (ax_avg_ms * 1e-3) / 1e12
-        roof_alu = {"bound": "alu", "achieved": ach, "peak": metrics.FP32_PEAK_TOPS,
-                    "unit": "T FP32 instr/s", "frac": ach / metrics.FP32_PEAK_TOPS, "traffic": traffic,
-                    "peak_source": "152 SMs x 128 FP32 lanes x 2070 MHz (derived, nominal clock)",
+        roof_alu = {"bound": "alu", "achieved": ach, "peak": fp32_peak,
+                    "unit": "T FP32 instr/s", "frac": ach / fp32_peak, "traffic": traffic,
+                    "peak_source": "measured: nb_fp32_rate (FFMA rate, all SMs, this run); nominal "
+                                   f"152 SMs x 128 lanes x 2070 MHz = {metrics.FP32_PEAK_TOPS:.2f}",
                     "kernel": "ax_e (CG head)", "algorithmic_fp32_instr_per_launch": ops,
                     "avg_launch_ms": ax_avg_ms, "launches": ax["launches"]}
     else:
@@ -489,12 +568,16 @@ def run_gpu(args, rank, world, local):
         "kernel_share": {k: v["ms_total"] / total_kernel_ms for k, v in kern.items() if total_kernel_ms},
         "value_graph_mode": value_graph,
         "eq1_gflops": value * metrics.cg_flops_per_point(NGLL),
-        "paper_units_gbs": value * metrics.cg_bytes_per_point(),
+        "eq2_accounting_gbs": value * metrics.cg_bytes_per_point(),
+        "eq2_accounting_note": "GDOF/s x the paper's 240 B per point per CG iteration (Eq. 2); the "
+                               "fused iteration moves about 120 B per point, so this is not a "
+                               "roofline fraction",
         "ax_only": {"ms": t_ax, "gdofs": D / (t_ax * 1e-3) / 1e9,
                     "hbm_frac": metrics.ax_bytes_per_point(8) * D / (t_ax * 1e-3) / 1e9 / hbm,
                     "l2": "flushed between reps"},
         "ax_dssum": {"ms": t_axds, "gdofs": D / (t_axds * 1e-3) / 1e9},
         "ax_sweep_n10": sweep,
+        "config1_4x4x4_n8_cg100": config1,
         "ax_only_native_fp64": {"ms": t_ax_fp64, "gdofs": D / (t_ax_fp64 * 1e-3) / 1e9,
                                 "fp64_tflops": metrics.ax_flops_per_point(NGLL) * D / (t_ax_fp64 * 1e-3) / 1e12},
         "e2e": {"value": value_e2e, "unit": "GDOF/s",

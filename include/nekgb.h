@@ -368,6 +368,14 @@ nb_status nb_timing_enable(nb_ctx *ctx, int on);
 nb_status nb_timing_read(nb_ctx *ctx, int kernel_id, double *ms_total,
                          int64_t *launches, int reset);
 
+/* Measured FP32 instruction rate of the current device (FFMA per second,
+ * all SMs, 16 independent chains per thread, best of 5 timed runs after a
+ * warm-up; about 30 ms).  The paper has no counterpart: its roofline is
+ * bandwidth-only (Sec. V, Eq. 2).  This is the ceiling of the double-float
+ * ax_e, whose work is FP32 instructions.  Allocates and frees a small
+ * scratch buffer and a private stream; synchronous. */
+nb_status nb_fp32_rate(double *ffma_per_s);
+
 /* --------------------------------------------------------------------- */
 /* Status                                                                */
 /* --------------------------------------------------------------------- */

@@ -143,6 +143,13 @@ static nb_status new_ctx(nb_ctx **out, nb_box mesh, int n, nb_precision prec, vo
     {
         const char *st = getenv("NEKGB_F32_STAGED");
         c->f32_plain = st && st[0] == '0';
+        // tests of the bounded-wait path: the staged FP32 head's first wait
+        // runs out after this many nanoseconds (0 or unset: normal waits)
+        const char *tw = getenv("NEKGB_TEST_UNARMED_WAIT_NS");
+        c->test_unarmed_wait_ns = tw ? strtoull(tw, nullptr, 10) : 0ull;
+        // tests of the exact <w,p>_c sum's range check: shift its scale
+        const char *ds = getenv("NEKGB_TEST_DOT_SHIFT");
+        c->test_dot_shift = ds ? atoi(ds) : 0;
     }
     *out = c;
     return NB_OK;

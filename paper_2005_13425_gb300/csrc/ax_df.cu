@@ -41,6 +41,7 @@ struct AxDfArgs {
     double *partials;     // MODE 1 fused: one <w,p> partial per CTA
     int finalize;         // MODE 1 fused: the last CTA reduces <w,p>_c and forms alpha
     int dot_shift0;       // MODE 1 two-kernel CG: scale of the exact <w,p>_c sum (see launch_df_nv)
+    int dot_lim;          // MODE 1 two-kernel CG: a share of 2^dot_lim or more (scaled) may overflow the sum
     int fuse;             // MODE 1: zero box-face points, local products w p
     Mesh m;
     const float2 *g;      // gxyz pairs [E][6][n^3], scaled by 2^-(gexp-1023)
@@ -52,12 +53,16 @@ struct AxDfArgs {
 using u128 = unsigned __int128;
 
 // v 2^S truncated toward zero to an integer, as a two's-complement 128-bit
-// value.  The caller's S keeps |v| 2^S below 2^(126 - ...) (see the head), so
-// the shift never passes 73; values whose scaled magnitude is below 1 give 0.
-__device__ __forceinline__ u128 fixed_of(double v, int S) {
+// value.  The caller's S keeps |v| 2^S below 2^lim (lim = 125 - log2 of the
+// number of shares, see the head), so no sum of shares overflows; a share
+// that may reach 2^lim sets `out_of_range` (the solve then stops with a
+// status instead of using a wrong sum).  The shift is clamped at 73; values
+// whose scaled magnitude is below 1 give 0.
+__device__ __forceinline__ u128 fixed_of(double v, int S, int lim, bool &out_of_range) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int ex = (int)((b >> 52) & 0x7ff);
     if (ex == 0) return 0;
+    out_of_range |= ex - 1022 + S > lim;                 // |v| 2^S < 2^(ex - 1022 + S)
     const unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);
     int sh = ex - 1075 + S;
     u128 mag;
@@ -134,7 +139,8 @@ __device__ __forceinline__ double scale2(double x, int k) {
 // (see launch_df_nv); the result is rounded to FP64 once, at the end.
 template <int N, bool EO>
 __device__ __forceinline__ u128 cg_head_pipelined(const AxDfArgs &a, double beta, double xa, int S,
-                                                  const typename DfConsts<N, EO>::type &D, float2 *sm) {
+                                                  const typename DfConsts<N, EO>::type &D, float2 *sm,
+                                                  bool &out_of_range) {
     constexpr int N2 = N * N, N3 = N * N * N;
     constexpr int T = ax_df_threads(N);
     __shared__ long long s_next;
@@ -243,7 +249,7 @@ __device__ __forceinline__ u128 cg_head_pipelined(const AxDfArgs &a, double beta
                     de = fma(wv, p[q], de);
                 w[q] = wv;
             }
-            acc += fixed_of(de, S);
+            acc += fixed_of(de, S, a.dot_lim, out_of_range);
         }
         const int64_t en = s_next;
         if (en < a.E) stage(en, odd ? S0 : S1);
@@ -272,9 +278,15 @@ ax_df_kernel(AxDfArgs a, const __grid_constant__ typename DfConsts<N, EO>::type 
         // the exact sums: per CTA, then over the CTAs by the last one
         const double pn = a.sc->it == 0 ? a.sc->rr : a.sc->pn2;
         const int S = a.dot_shift0 - ((int)((__double_as_longlong(pn) >> 52) & 0x7ff) - 1023);
-        const u128 mine = block_sum_u128(cg_head_pipelined<N, EO>(a, beta, xa, S, D, sm), red);
+        bool out_of_range = false;
+        const u128 mine = block_sum_u128(cg_head_pipelined<N, EO>(a, beta, xa, S, D, sm, out_of_range), red);
+        const int range_fault = __syncthreads_or(out_of_range);
         __shared__ int s_last;
         if (threadIdx.x == 0) {
+            if (range_fault) {           // seen by the last CTA's finalize_alpha, which ends the solve
+                a.sc->fault = kFaultExactSumRange;
+                a.sc->status = (int)NB_ERR_BREAKDOWN;
+            }
             a.partials[2 * blockIdx.x] = __longlong_as_double((long long)(unsigned long long)(mine >> 64));
             a.partials[2 * blockIdx.x + 1] = __longlong_as_double((long long)(unsigned long long)mine);
             __threadfence();
@@ -398,6 +410,9 @@ bool centro_antisymmetric(const double *D, int n) {
 // stays below 2^(sa + e + S + log2(E T)) <= 2^125: no 128-bit sum overflows.
 // The grid of the sum, 2^-S, is 2^-(125 - log2(E T)) of that bound.
 template <int N>
+static int dot_lim(const nb_ctx *c);
+
+template <int N>
 static int dot_shift0(const nb_ctx *c) {
     constexpr int T = ax_df_threads(N);
     constexpr int P = (N * N * N + T - 1) / T;
@@ -413,8 +428,15 @@ static int dot_shift0(const nb_ctx *c) {
     }
     // max|G| < 2^(gexp - 1022)
     const int sa = (int)ceil(log2(72.0 * P * 9.0 * d1 * dinf)) + (c->gxyz_exp - 1022) + 1 + 4;
-    const int sE = (int)ceil(log2((double)c->m.E * T));
-    return 125 - sE - sa;
+    return dot_lim<N>(c) - sa;
+}
+
+// The bound of one scaled share: 2^(125 - log2(E T)), so that E T shares
+// sum below 2^125.
+template <int N>
+static int dot_lim(const nb_ctx *c) {
+    constexpr int T = ax_df_threads(N);
+    return 125 - (int)ceil(log2((double)c->m.E * T));
 }
 
 template <int N, bool EO>
@@ -443,7 +465,8 @@ static nb_status launch_df_nv(nb_ctx *c, const double *u, double *w, int mode) {
         args.partials = c->d_partials;
         args.fuse = c->fused_cg ? 1 : 0;
         args.finalize = c->two_kernel ? 1 : 0;
-        args.dot_shift0 = dot_shift0<N>(c);
+        args.dot_shift0 = dot_shift0<N>(c) + c->test_dot_shift;
+        args.dot_lim = dot_lim<N>(c);
     }
     args.m = c->m;
     auto kern = mode == 0 ? ax_df_kernel<N, 0, EO> : ax_df_kernel<N, 1, EO>;

@@ -25,6 +25,8 @@ struct AxF32Args {
     Mesh m;
     const float *g;       // gxyz [E][6][n^3], FP32
     int64_t E;
+    uint64_t unarmed_wait_ns;  // staged kernel, tests only: 0, or the limit of a first wait on a
+                               // barrier nothing arrives on (exercises the timeout path)
 };
 
 // MODE 0: w = ax_e(u).  MODE 1: inner CG head (x += x_alpha p, p = r + beta
@@ -74,7 +76,10 @@ ax_f32_kernel(AxF32Args a, const __grid_constant__ F32Mat<N> D) {
 // f32_element_staged): thread 0 arms the next element's barrier and issues
 // its copies, every thread waits (bounded) for the current one.  A copy
 // that does not complete within ~1 s ends the kernel with NB_ERR_TIMEOUT in
-// the scalar block (err), after draining the copies in flight.
+// the scalar block (err), after draining the copies in flight.  With
+// unarmed_wait_ns (a context set up with NEKGB_TEST_UNARMED_WAIT_NS, for
+// tests) each CTA's first wait is made on a barrier that nothing arrives on,
+// with that limit: it runs out, and the same drain-and-report path runs.
 template <int N, int MODE>
 __global__ void __launch_bounds__(ax_f32_threads(N))
 ax_f32_staged_kernel(AxF32Args a, CgScalars *err, const __grid_constant__ F32Mat<N> D) {
@@ -83,7 +88,7 @@ ax_f32_staged_kernel(AxF32Args a, CgScalars *err, const __grid_constant__ F32Mat
     constexpr int STAGE = f32_stage_floats<N, MODE>();
     extern __shared__ __align__(16) float smf[];
     __shared__ double red[32];
-    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(8) uint64_t bars[3];   // bars[2] is never armed (unarmed_wait_ns)
     float beta = 0.f, xa = 0.f;
     dfa::Acc32 dot;
     if (MODE == 1) {
@@ -95,6 +100,7 @@ ax_f32_staged_kernel(AxF32Args a, CgScalars *err, const __grid_constant__ F32Mat
     if (t == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -127,7 +133,9 @@ ax_f32_staged_kernel(AxF32Args a, CgScalars *err, const __grid_constant__ F32Mat
             if (t == 0) issue(en, s ^ 1);
             issued[s ^ 1]++;
         }
-        ok = __syncthreads_and(mbar_wait(&bars[s], waited[s] & 1)) != 0;
+        const bool unarmed = a.unarmed_wait_ns != 0 && i == 0;
+        ok = __syncthreads_and(unarmed ? mbar_wait(&bars[2], 0, a.unarmed_wait_ns)
+                                       : mbar_wait(&bars[s], waited[s] & 1)) != 0;
         if (!ok) break;
         waited[s]++;
         F32StagedOut o;
@@ -174,6 +182,7 @@ static nb_status launch_f32_n(nb_ctx *c, const float *u, float *w, int mode) {
     args.g = c->d_gxyz32;
     args.E = c->m.E;
     args.m = c->m;
+    args.unarmed_wait_ns = c->test_unarmed_wait_ns;
     if (mode == 0) {
         args.u = u;
         args.w = w;

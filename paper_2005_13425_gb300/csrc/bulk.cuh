@@ -86,13 +86,14 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Wait for the barrier's phase with the given parity to complete; false
-// after ~1 s without completion.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+// after limit_ns (default ~1 s) without completion.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity,
+                                          uint64_t limit_ns = 1000000000ull) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > 1000000000ull) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
 

@@ -438,6 +438,8 @@ nb_status cg_solve_fp64(nb_ctx *c, const double *f, double *x, double tol, int m
     if (iters) *iters = h.it;
     const double rel = h.fnorm2 > 0.0 ? sqrt(h.rr) / sqrt(h.fnorm2) : 0.0;
     if (relres) *relres = rel;
+    if (h.status == (int)NB_ERR_BREAKDOWN && h.fault == kFaultExactSumRange)
+        return fail(NB_ERR_BREAKDOWN, "the exact <w,p>_c sum left its range (its scale comes from the <p,p>_c recursion)");
     if (h.status == (int)NB_ERR_BREAKDOWN) return fail(NB_ERR_BREAKDOWN, "CG breakdown: <Ap,p>_c <= 0 or not finite");
     if (tol > 0.0 && !(rel <= tol) && h.rr != 0.0)
         return fail(NB_ERR_NOT_CONVERGED, "CG did not reach the tolerance within maxit");

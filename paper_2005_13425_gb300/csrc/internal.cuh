@@ -76,6 +76,10 @@ inline Mesh make_box_mesh(int ex, int ey, int ez, int n) {
 
 // ---------------------------------------------------------------- CG state
 // Device-resident scalars of one CG solve.
+// CgScalars::fault: a scaled share of the FP64 CG head's exact <w,p>_c sum
+// reached the bound that keeps the 128-bit sum from overflowing.
+constexpr int kFaultExactSumRange = 1;
+
 struct CgScalars {
     double rho;        // <r,z>_c (z = r without a preconditioner, minv r with Jacobi)
     double rr;         // <r,r>_c (convergence test and history)
@@ -89,7 +93,8 @@ struct CgScalars {
     int it;            // iterations completed
     int maxit;
     int done;          // 1: no further iteration runs
-    int status;        // 0 ok, NB_ERR_BREAKDOWN
+    int status;        // 0 ok, NB_ERR_BREAKDOWN, NB_ERR_TIMEOUT
+    int fault;         // detail of a BREAKDOWN status: 0, or kFaultExactSumRange
     unsigned int ticket;  // last-block-done counter for reductions
     unsigned int next_elem;  // element counter of the CG head's dynamic schedule (reset by its last CTA)
 };
@@ -141,6 +146,8 @@ struct nb_ctx {
     int cg_graph32_chunk = 0;
     // mixed-precision parameters and statistics
     bool f32_plain = false;             // FP32 ax_e without bulk staging (NEKGB_F32_STAGED=0)
+    unsigned long long test_unarmed_wait_ns = 0;   // NEKGB_TEST_UNARMED_WAIT_NS (tests of the timeout path)
+    int test_dot_shift = 0;             // NEKGB_TEST_DOT_SHIFT: added to the exact sum's scale (tests of its range check)
     double mixed_inner_tol = 1e-4;
     int mixed_max_outer = 50;
     int last_outer = 0;

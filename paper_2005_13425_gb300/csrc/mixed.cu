@@ -242,7 +242,7 @@ nb_status cg_solve_mixed(nb_ctx *c, const double *f, double *x, double tol, int 
         const int done_inner = c->h_sc->it;
         inner_total += done_inner;
         outer += 1;
-        if (c->h_sc->status == (int)NB_ERR_BREAKDOWN || done_inner == 0) break;
+        if (c->h_sc->status != 0 || done_inner == 0) break;
     }
     NB_CUDA(cudaMemcpyAsync(x, c->d_x, bytes, cudaMemcpyDeviceToDevice, c->stream));
     NB_CUDA(cudaStreamSynchronize(c->stream));
@@ -251,6 +251,8 @@ nb_status cg_solve_mixed(nb_ctx *c, const double *f, double *x, double tol, int 
     c->last_outer = outer;
     if (iters) *iters = inner_total;
     if (relres) *relres = rel;
+    if (c->h_sc->status == (int)NB_ERR_TIMEOUT)
+        return fail(NB_ERR_TIMEOUT, "a bounded device wait of the FP32 head ran out (copies drained)");
     if (c->h_sc->status == (int)NB_ERR_BREAKDOWN && !converged)
         return fail(NB_ERR_BREAKDOWN, "inner CG breakdown: <Ap,p>_c <= 0 or not finite");
     if (tol > 0.0 && !converged) return fail(NB_ERR_NOT_CONVERGED, "defect correction did not reach tol");

@@ -66,7 +66,13 @@ __device__ bool last_block_reduce(const double (&v)[NV], double *partials, int s
 // flag when <w,p>_c <= 0 or is not finite (the owed x update is dropped).
 __device__ __forceinline__ void finalize_alpha(CgScalars *sc, double pap) {
     sc->pap = pap;
-    if (!(pap > 0.0) || !isfinite(pap)) {
+    // an error status set by another CTA of this kernel (a bounded wait that
+    // ran out, the exact sum's range check) ends the solve; read past L1,
+    // which may hold the scalar block's line from the kernel's start
+    if (__ldcg(&sc->status) != 0) {
+        sc->done = 1;
+        sc->x_alpha = 0.0;
+    } else if (!(pap > 0.0) || !isfinite(pap)) {
         sc->status = (int)NB_ERR_BREAKDOWN;
         sc->done = 1;
         sc->x_alpha = 0.0;

@@ -18,8 +18,10 @@ FALLBACK_HBM_GBS = 6800.0
 FALLBACK_BF16_TFLOPS = 1900.0
 # FP64 ALU ceiling: the nominal GB300 FP64 rate (TFLOP/s).
 NOMINAL_FP64_TFLOPS = 1.25
-# FP32-pipe ceiling of GB300: 152 SMs x 128 FP32 lanes x 2070 MHz maximum
-# SM clock, one FADD, FMUL or FFMA per lane per clock (10^12 instr/s).
+# Nominal FP32-pipe ceiling of GB300: 152 SMs x 128 FP32 lanes x 2070 MHz
+# maximum SM clock, one FADD, FMUL or FFMA per lane per clock (10^12
+# instr/s).  The ALU roofline uses the rate measured on the device
+# (nb_fp32_rate); this is the context figure.
 GB300_SMS = 152
 FP32_LANES_PER_SM = 128
 MAX_SM_MHZ = 2070.0
@@ -132,17 +134,16 @@ def source_digest(csrc_dir: str, names=CG_HEAD_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(profile_path: str, digest: str):
-    """DRAM bytes per launch recorded in a profile summary (lines
-    'source_digest: <hex>' and 'traffic_bytes_per_launch: <int>'), or None
-    when the file is missing or was measured on other sources."""
+def recorded_traffic(data_path: str, kernel: str, digest: str):
+    """DRAM bytes per launch of `kernel` recorded in the profiles' data file
+    (JSON: {"kernels": {kernel: {"source_digest": hex,
+    "dram_bytes_per_launch": int, ...}}}), or None when the file or the
+    entry is missing or was measured on other sources."""
     try:
-        with open(profile_path) as fh:
-            text = fh.read()
-    except OSError:
+        with open(data_path) as fh:
+            rec = json.load(fh)["kernels"][kernel]
+        if rec["source_digest"] != digest:
+            return None
+        return int(rec["dram_bytes_per_launch"])
+    except (OSError, KeyError, TypeError, ValueError):
         return None
-    d = re.search(r"^source_digest:\s*([0-9a-f]+)\s*$", text, re.M)
-    t = re.search(r"^traffic_bytes_per_launch:\s*([0-9]+)\s*$", text, re.M)
-    if not d or not t or d.group(1) != digest:
-        return None
-    return int(t.group(1))

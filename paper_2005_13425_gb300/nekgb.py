@@ -98,6 +98,7 @@ _SIGS = {
     "nb_engine_tuning": [_vp, ctypes.c_int, ctypes.c_int, _ip, _ip],
     "nb_timing_enable": [_vp, ctypes.c_int],
     "nb_timing_read": [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
+    "nb_fp32_rate": [_dp],
 }
 
 
@@ -331,6 +332,13 @@ def nb_timing_read(ctx, kernel_id: int, reset: bool = False):
     _check(load().nb_timing_read(ctx, int(kernel_id), ctypes.byref(ms), ctypes.byref(cnt),
                                  1 if reset else 0), "nb_timing_read")
     return ms.value, cnt.value
+
+
+def nb_fp32_rate() -> float:
+    """Measured FFMA (FP32 instruction) rate of the current device, per second."""
+    v = ctypes.c_double(0.0)
+    _check(load().nb_fp32_rate(ctypes.byref(v)), "nb_fp32_rate")
+    return v.value
 
 
 # ------------------------------------------------------------------ engine

@@ -7,7 +7,10 @@ batched_run: every problem of a list is admitted, then all advance together
     by a fixed number of CG iterations (the paper's fixed-iteration mode,
     Sec. V); throughput = sum of E n^3 x iterations / device time.  The same
     problems solved one after another through the engine give the
-    sequential reference.
+    sequential reference.  Mixed requests are stepped until every one has
+    used its inner-iteration budget (an inner solve that ends inside a step
+    waits for the next step's outer pass), and throughput counts the inner
+    iterations each request completed.
 serving_run: requests arrive as a Poisson process; a request is admitted as
     soon as its footprint fits in the free arena (first come, first served),
     all admitted requests advance together in steps of a few iterations, and
@@ -34,7 +37,9 @@ def batched_run(nekgb, stream, probs, iters=100, sequential=True, prec=0):
     """Fixed-iteration batched solve of `probs` (dicts with dims, n,
     mesh_seed, f_seed).  Returns throughput numbers.  With prec = NB_MIXED
     the iterations are inner (FP32) iterations of the defect correction, the
-    problems run with tol = 0, so they never stop early."""
+    problems run with tol = 0, so they never stop early; the engine is
+    stepped in chunks until every request is done and the GDOF/s counts the
+    inner iterations each request completed."""
     import torch
     need = footprint_total(nekgb, probs, prec)
     eng = nekgb.nb_engine_create(int(need * 1.1) + (64 << 20), stream)
@@ -60,14 +65,28 @@ def batched_run(nekgb, stream, probs, iters=100, sequential=True, prec=0):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         stream.synchronize()
         a.record(stream)
-        nekgb.nb_engine_step(eng, iters)
+        steps = 0
+        if prec == 0:
+            nekgb.nb_engine_step(eng, iters)
+            steps = 1
+        else:
+            for steps in range(1, 4 * iters + 1):
+                nekgb.nb_engine_step(eng, 8)
+                if all(nekgb.nb_engine_poll(eng, rid)[0] for rid in ids):
+                    break
         b.record(stream)
         b.synchronize()
         ms = a.elapsed_time(b)
         dofs = sum(p["E"] * p["n"] ** 3 for p in probs)
-        done = all(nekgb.nb_engine_poll(eng, rid)[0] for rid in ids)
-        out.update({"ms": ms, "local_dofs": dofs, "all_done": done,
-                    "gdofs": dofs * iters / (ms * 1e-3) / 1e9})
+        polls = [nekgb.nb_engine_poll(eng, rid) for rid in ids]
+        done = all(pl[0] for pl in polls)
+        done_its = [pl[1] for pl in polls]
+        dof_its = sum(p["E"] * p["n"] ** 3 * it for p, it in zip(probs, done_its))
+        out.update({"ms": ms, "local_dofs": dofs, "all_done": done, "engine_steps": steps,
+                    "iterations_completed_min": min(done_its), "iterations_completed_max": max(done_its),
+                    "gdofs": dof_its / (ms * 1e-3) / 1e9})
+        if prec != 0:
+            out["outer_passes_mean"] = float(np.mean([nekgb.nb_engine_request_info(eng, rid)[1] for rid in ids]))
         for rid in ids:
             nekgb.nb_engine_retire(eng, rid)
         if sequential:

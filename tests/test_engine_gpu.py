@@ -223,3 +223,31 @@ def test_engine_staged_f32_head_matches_plain(nek, oracle):
     for a, b in zip(*outs):
         assert a[1] == b[1] and a[2] == b[2] and a[4] == b[4] and a[3] == nek.NB_OK
         assert np.array_equal(a[0], b[0])
+
+
+def test_engine_batch_at_full_sizes_against_oracle(nek, oracle):
+    """The batched engine at the sizes the 256-problem list draws: 16^3
+    elements at n = 10 and 8^3 at n = 12 (the largest E and n), with small
+    problems of other n in the same batch.  FP64 requests run 30 fixed
+    iterations and are compared with the oracle's CG (rho history and x to
+    1e-8, CG's reduction-order amplification); mixed requests of the two
+    large problems reach relative residual 1e-10 in the oracle's operator."""
+    big = [((16, 16, 16), 10), ((8, 8, 8), 12)]
+    small = [((2, 2, 2), 6), ((4, 2, 2), 8)]
+    items, probs = [], []
+    for pid, (dims, n) in enumerate(big + small):
+        P, s, f = problem(oracle, dims, n, 120 + pid)
+        probs.append((dims, n, P, f))
+        items.append((dims, n, s, f, 0.0, 30, nek.NB_FP64))
+    for pid, (dims, n) in enumerate(big):
+        _, s, f = problem(oracle, dims, n, 120 + pid)
+        items.append((dims, n, s, f, 1e-10, 20000, nek.NB_MIXED))
+    out = run_engine(nek, items, arena=16 * GIB, iters_per_step=32)
+    for (dims, n, P, f), (x, it, rr, st, _) in zip(probs, out[:len(probs)]):
+        x_ref, it_ref, rr_ref, _, _ = oracle.cg(*dims, n, P["D"], P["gxyz"], P["mask"], f, tol=0.0, maxit=30)
+        assert st == nek.NB_OK and it == 30 == it_ref
+        assert np.abs(x - x_ref).max() <= 1e-8 * np.abs(x_ref).max()
+        assert abs(rr - rr_ref) <= 1e-8 * rr_ref
+    for (dims, n, P, f), (x, it, rr, st, outer) in zip(probs, out[len(probs):]):
+        assert st == nek.NB_OK and rr <= 1e-10 and outer >= 2
+        assert true_relres(oracle, dims, n, P, f, x) <= 2e-10

@@ -53,11 +53,24 @@ def test_double_float_op_counts():
 
 
 def test_recorded_traffic_needs_matching_digest(tmp_path):
-    p = tmp_path / "prof.md"
-    p.write_text("# summary\nsource_digest: abcdef0123456789\ntraffic_bytes_per_launch: 393216000\n")
-    assert metrics.recorded_traffic(str(p), "abcdef0123456789") == 393216000
-    assert metrics.recorded_traffic(str(p), "0000000000000000") is None
-    assert metrics.recorded_traffic(str(tmp_path / "missing.md"), "abcdef0123456789") is None
+    import json
+    p = tmp_path / "traffic.json"
+    p.write_text(json.dumps({"kernels": {"head": {"source_digest": "abcdef0123456789",
+                                                  "dram_bytes_per_launch": 393216000}}}))
+    assert metrics.recorded_traffic(str(p), "head", "abcdef0123456789") == 393216000
+    assert metrics.recorded_traffic(str(p), "head", "0000000000000000") is None
+    assert metrics.recorded_traffic(str(p), "other", "abcdef0123456789") is None
+    assert metrics.recorded_traffic(str(tmp_path / "missing.json"), "head", "abcdef0123456789") is None
+
+
+def test_committed_traffic_file_is_well_formed():
+    import json
+    path = os.path.join(os.path.dirname(os.path.dirname(__file__)), "profiles", "traffic.json")
+    rec = json.load(open(path))["kernels"]
+    assert rec
+    for k, v in rec.items():
+        assert len(v["source_digest"]) == 16 and int(v["dram_bytes_per_launch"]) > 0, k
+        assert os.path.exists(os.path.join(os.path.dirname(path), v["profile"])), k
 
 
 def test_source_digest_ignores_comments_only(tmp_path):

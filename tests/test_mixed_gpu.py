@@ -185,3 +185,34 @@ def test_f32_staged_operator_and_solve_match_plain(nek, oracle, dims, n):
     err = np.abs(w1.astype(np.float64) - want).max() / np.abs(want).max()
     assert err <= 2e-5, err
     assert rr1 <= 1e-10
+
+
+@pytest.mark.parametrize("n", [8, 10])
+def test_config3_full_size_against_oracle(nek, oracle, n):
+    """The mixed configuration at its own size: E = 4096 (16 x 16 x 16),
+    n = 8 and 10, manufactured solution u* = sin(pi x) sin(pi y) sin(pi z)
+    with f = A u* from the FP64 oracle on the oracle's mesh; defect
+    correction to relative residual 1e-10.  Checked: the FP64 relative
+    residual of the result recomputed by the oracle, and its error against
+    u* and against the oracle's own FP64 CG solution (both within
+    kappa * 1e-10 of the exact discrete solution)."""
+    dims = (16, 16, 16)
+    P, us, f = manufactured(oracle, dims, n, seed=inputs.SEED_MESH)
+    x_ref, it_ref, rr_ref, _, st_ref = oracle.cg(*dims, n, P["D"], P["gxyz"], P["mask"], f,
+                                                  tol=1e-10, maxit=20000)
+    assert st_ref == 0 and rr_ref <= 1e-10
+    h = mixed_ctx(nek, P, dims, n)
+    try:
+        x = torch.zeros_like(dev(f))
+        st, it, rr = nek.nb_cg_solve(h, dev(f), x, tol=1e-10, maxit=20000)
+        _, outer = nek.nb_solve_stats(h)
+        xm = host(x)
+    finally:
+        nek.nb_destroy(h)
+    assert st == nek.NB_OK and rr <= 1e-10 and outer >= 2
+    r = f - oracle.apply_A(*dims, n, P["D"], P["gxyz"], P["mask"], xm)
+    true_rel = np.sqrt(oracle.dot_c(*dims, n, r, r) / oracle.dot_c(*dims, n, f, f))
+    assert true_rel <= 1.5e-10, true_rel
+    umax = np.abs(us).max()
+    assert np.abs(xm - us).max() <= 1e-7 * umax
+    assert np.abs(xm - x_ref).max() <= 1e-7 * umax

@@ -14,7 +14,8 @@ the oracle alone:
   16 of error in it.
 Measured here: max|A_e p| reaches 0.5-2.6 % of the operator bound (it is a
 safe bound, which is the direction that matters), and the recursion matches
-the true <p,p>_c to 1e-13 relative over 100 iterations.
+the true <p,p>_c to 2e-12 relative over 1500 iterations, through
+convergence and 18 orders of magnitude of residual beyond it.
 """
 import numpy as np
 import pytest
@@ -51,9 +52,13 @@ def test_element_operator_bound(oracle, n):
 
 
 def test_search_direction_norm_recursion(oracle):
-    """100 CG iterations (oracle operator, weighted dot): the recursion for
-    <p,p>_c stays within 1 % of the true value (the head allows a factor 16)."""
-    dims, n = (4, 4, 3), 8
+    """1500 CG iterations (oracle operator, weighted dot) on a problem that
+    converges after about 600, so the run covers both the convergence phase
+    and the round-off phase beyond it (relative residual down to ~1e-28): the
+    recursion for <p,p>_c stays within 1 % of the true value (the head allows
+    a factor 16).  Solves of the benchmark's problem take 850-1150
+    iterations to 1e-10."""
+    dims, n = (8, 8, 4), 10
     P = oracle.box_problem(*dims, n, inputs.PERTURB_AMP, inputs.perturbation_coeffs(0))
     f = oracle.apply_mask(P["mask"], oracle.scatter_unique(*dims, n, inputs.unique_field(*dims, n, 1)))
     dot = lambda a, b: oracle.dot_c(*dims, n, a, b)
@@ -62,7 +67,8 @@ def test_search_direction_norm_recursion(oracle):
     p = np.zeros_like(f)
     rho_old, pn2 = 1.0, 0.0
     worst = 1.0
-    for it in range(100):
+    f2 = dot(f, f)
+    for it in range(1500):
         rho = dot(r, r)
         beta = 0.0 if it == 0 else rho / rho_old
         p = r + beta * p
@@ -73,4 +79,5 @@ def test_search_direction_norm_recursion(oracle):
         alpha = rho / dot(w, p)
         r = r - alpha * w
         rho_old = rho
+    assert np.sqrt(rho / f2) < 1e-20          # well past convergence
     assert worst <= 1.01
