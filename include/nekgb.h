@@ -368,6 +368,53 @@ nb_status nb_timing_enable(nb_ctx *ctx, int on);
 nb_status nb_timing_read(nb_ctx *ctx, int kernel_id, double *ms_total,
                          int64_t *launches, int reset);
 
+/* --------------------------------------------------------------------- */
+/* Partitioned box: slabs of element layers along z                       */
+/* --------------------------------------------------------------------- */
+/* Nekbone distributes elements over processes (Sec. I-II); the second step
+ * of Ax sums element results into the shared nodes (Sec. III), which across
+ * a partition is an exchange between neighbouring slabs.  A slab context
+ * holds the element layers z0 .. z1-1 of the global box `global` (geometry
+ * built on the device at the global coordinates, the Dirichlet mask of the
+ * global boundary, FP64-accurate).  nb_ax, nb_dssum (slab-local) and
+ * nb_mask work on it; nb_apply, nb_dot_c and the CG solves return
+ * NB_ERR_STATE (they need the neighbours' copies).  The assembled operator
+ * of the whole box, bit for bit equal to the single-box dssum, is
+ *   w = ax(p) on every slab;
+ *   nb_slab_top_partial(w, up)         -> send up[] to the slab above;
+ *   nb_slab_add_bottom(w, from_below)  (slabs with a slab below);
+ *   nb_dssum(w);
+ *   nb_slab_bottom_value(w, down)      -> send down[] to the slab below;
+ *   nb_slab_set_top(w, from_above)     (slabs with a slab above);
+ *   nb_mask(w).
+ * Plane buffers are device arrays of plane_nodes = (ex(n-1)+1)(ey(n-1)+1)
+ * doubles (x fastest).  All calls are asynchronous on the context's stream
+ * except nb_slab_dot.  Errors: NB_ERR_ARG (sizes, NULL or misaligned
+ * pointers), NB_ERR_STATE (not a slab context), NB_ERR_CUDA. */
+nb_status nb_setup_slab(nb_ctx **out, nb_box global, int z0, int z1, int n,
+                        double amp, const double *s, void *cuda_stream);
+/* Plane size and whether the slab has neighbours below (z0 > 0) and above. */
+nb_status nb_slab_info(nb_ctx *ctx, int64_t *plane_nodes, int *has_below,
+                       int *has_above);
+/* buf[node] = the slab's copies of each top-plane node summed from +0.0 in
+ * ascending element order (w as ax_e left it, before any dssum). */
+nb_status nb_slab_top_partial(nb_ctx *ctx, const double *w_dev, double *buf_dev);
+/* The first (lowest element) copy of each bottom-plane node += buf[node]:
+ * the sum continues from the slab below's partial. */
+nb_status nb_slab_add_bottom(nb_ctx *ctx, double *w_dev, const double *buf_dev);
+/* buf[node] = the assembled value of each bottom-plane node (after nb_dssum). */
+nb_status nb_slab_bottom_value(nb_ctx *ctx, const double *w_dev, double *buf_dev);
+/* Every copy of each top-plane node := buf[node] (the value from above). */
+nb_status nb_slab_set_top(nb_ctx *ctx, double *w_dev, const double *buf_dev);
+/* *out_host = the slab's share of <a,b>_c with the global multiplicities
+ * (the shares of all slabs add up to the whole box's <a,b>_c).  Blocks. */
+nb_status nb_slab_dot(nb_ctx *ctx, const double *a_dev, const double *b_dev,
+                      double *out_host);
+/* y = alpha x + beta y over the context's local points (any context);
+ * beta = 0 does not read y. */
+nb_status nb_axpby(nb_ctx *ctx, double alpha, const double *x_dev, double beta,
+                   double *y_dev);
+
 /* Measured FP32 instruction rate of the current device (FFMA per second,
  * all SMs, 16 independent chains per thread, best of 5 timed runs after a
  * warm-up; about 30 ms).  The paper has no counterpart: its roofline is

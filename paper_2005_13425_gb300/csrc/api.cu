@@ -102,7 +102,7 @@ nb_status harvest_timing(nb_ctx *c) {
     return NB_OK;
 }
 
-static nb_status check_mesh(nb_box mesh, int n) {
+nb_status check_mesh(nb_box mesh, int n) {
     if (n < 2 || n > kMaxN) return fail(NB_ERR_ARG, "n must be in 2..16");
     if (mesh.ex < 1 || mesh.ey < 1 || mesh.ez < 1)
         return fail(NB_ERR_ARG, "mesh dimensions must be >= 1");
@@ -114,7 +114,12 @@ static nb_status check_mesh(nb_box mesh, int n) {
 
 static bool aligned8(const void *p) { return ((uintptr_t)p & 7u) == 0; }
 
-static void free_ctx(nb_ctx *c) {
+// Whole-box operations that a slab context (nb_setup_slab) cannot do alone:
+// its interface nodes also have copies in the neighbouring slabs.
+static const char *const slab_refusal =
+    "a slab context covers part of the box: use the partitioned solve (nb_slab_* and an exchange between slabs)";
+
+void free_ctx(nb_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     void *ptrs[] = {c->d_D, c->d_gxyz, c->d_mask, c->d_Df, c->d_gxyz_df, c->d_gxyz32, c->d_minv,
@@ -133,7 +138,7 @@ static void free_ctx(nb_ctx *c) {
     delete c;
 }
 
-static nb_status new_ctx(nb_ctx **out, nb_box mesh, int n, nb_precision prec, void *stream) {
+nb_status new_ctx(nb_ctx **out, nb_box mesh, int n, nb_precision prec, void *stream) {
     nb_ctx *c = new (std::nothrow) nb_ctx();
     if (!c) return fail(NB_ERR_OOM, "host allocation of the context failed");
     c->m = make_box_mesh(mesh.ex, mesh.ey, mesh.ez, n);
@@ -324,6 +329,7 @@ nb_status nb_mask(nb_ctx *c, double *w) {
 
 nb_status nb_apply(nb_ctx *c, const double *u, double *w) {
     NB_GUARD_BEGIN
+    if (c && c->slab) return fail(NB_ERR_STATE, slab_refusal);
     nb_status s = nb_ax(c, u, w);
     if (s != NB_OK) return s;
     return launch_dssum(c, w, true);
@@ -334,6 +340,7 @@ nb_status nb_cg_solve(nb_ctx *c, const double *f, double *x, double tol, int max
                       double *relres) {
     NB_GUARD_BEGIN
     if (!c || !f || !x) return fail(NB_ERR_ARG, "NULL argument");
+    if (c->slab) return fail(NB_ERR_STATE, slab_refusal);
     if (!aligned8(f) || !aligned8(x)) return fail(NB_ERR_ARG, "pointers must be 8-byte aligned");
     if (maxit < 0) return fail(NB_ERR_ARG, "maxit must be >= 0");
     const size_t bytes = sizeof(double) * c->m.npts;
@@ -348,6 +355,7 @@ nb_status nb_cg_solve_host(nb_ctx *c, const double *f_host, double *x_host, doub
                            int *iters, double *relres) {
     NB_GUARD_BEGIN
     if (!c || !f_host || !x_host) return fail(NB_ERR_ARG, "NULL argument");
+    if (c->slab) return fail(NB_ERR_STATE, slab_refusal);
     nb_status s = ensure_cg_workspace(c);
     if (s != NB_OK) return s;
     const size_t bytes = sizeof(double) * c->m.npts;
@@ -392,6 +400,7 @@ nb_status nb_cg_history(nb_ctx *c, double *rho_host, int cap, int *count) {
 nb_status nb_dot_c(nb_ctx *c, const double *a, const double *b, double *out) {
     NB_GUARD_BEGIN
     if (!c || !a || !b || !out) return fail(NB_ERR_ARG, "NULL argument");
+    if (c->slab) return fail(NB_ERR_STATE, slab_refusal);
     return dot_c(c, a, b, out);
     NB_GUARD_END
 }

@@ -89,7 +89,15 @@ __device__ __forceinline__ void store_g(float2 *dst, double v) {
 struct GeomParams {
     double xi[kMaxN], w[kMaxN], D[kMaxN * kMaxN];
     double amp, s[3];
+    int ez0, ez_total;   // the mesh's elements are layers ez0.. of a box ez_total elements high
 };
+
+// A context's place in the z direction of its box (a slab of a partitioned
+// box starts at layer slab_z0 of slab_ez_global; a whole box at 0 of m.ez).
+static void z_extent(const nb_ctx *c, GeomParams &gp) {
+    gp.ez0 = c->slab ? c->slab_z0 : 0;
+    gp.ez_total = c->slab ? c->slab_ez_global : c->m.ez;
+}
 
 // One CTA per element (grid-stride).  Nodal coordinates are the affine box
 // position plus amp*s_d*sin(pi X) sin(pi Y) sin(pi Z); the Jacobian applies
@@ -108,7 +116,7 @@ __global__ void box_geometry_kernel(OutT *__restrict__ gxyz, Mesh m, GeomParams 
             const int a = threadIdx.x;
             X[a] = (ex + 0.5 * (gp.xi[a] + 1.0)) / m.ex;
             Y[a] = (ey + 0.5 * (gp.xi[a] + 1.0)) / m.ey;
-            Z[a] = (ez + 0.5 * (gp.xi[a] + 1.0)) / m.ez;
+            Z[a] = (ez + gp.ez0 + 0.5 * (gp.xi[a] + 1.0)) / gp.ez_total;
             SX[a] = sin(M_PI * X[a]);
             SY[a] = sin(M_PI * Y[a]);
             SZ[a] = sin(M_PI * Z[a]);
@@ -173,7 +181,7 @@ __global__ void box_coords_kernel(double *__restrict__ xyz, Mesh m, GeomParams g
         const int ex = (int)(e % m.ex), ey = (int)((e / m.ex) % m.ey), ez = (int)(e / ((int64_t)m.ex * m.ey));
         const double X = (ex + 0.5 * (gp.xi[i] + 1.0)) / m.ex;
         const double Y = (ey + 0.5 * (gp.xi[j] + 1.0)) / m.ey;
-        const double Z = (ez + 0.5 * (gp.xi[k] + 1.0)) / m.ez;
+        const double Z = (ez + gp.ez0 + 0.5 * (gp.xi[k] + 1.0)) / gp.ez_total;
         const double bump = sin(M_PI * X) * sin(M_PI * Y) * sin(M_PI * Z);
         double *o = xyz + e * 3 * n3 + p;
         o[0] = X + gp.amp * gp.s[0] * bump;
@@ -189,6 +197,7 @@ nb_status launch_box_coords(nb_ctx *c, double *xyz) {
     if (st != NB_OK) return st;
     gp.amp = c->box_amp;
     gp.s[0] = c->box_s[0]; gp.s[1] = c->box_s[1]; gp.s[2] = c->box_s[2];
+    z_extent(c, gp);
     const int sms = device_sms();
     box_coords_kernel<<<grid_blocks(c->m.npts, 256, sms * 8), 256, 0, c->stream>>>(xyz, c->m, gp);
     NB_LAUNCH_CHECK("box_coords_kernel");
@@ -203,6 +212,7 @@ nb_status launch_box_geometry(nb_ctx *c, double amp, const double *s, int *bad_d
     for (int q = 0; q < n * n; q++) gp.D[q] = c->D_host[q];
     gp.amp = amp;
     gp.s[0] = s[0]; gp.s[1] = s[1]; gp.s[2] = s[2];
+    z_extent(c, gp);
     const int sms = device_sms();
     const int grid = (int)(c->m.E < (int64_t)sms * 8 ? c->m.E : (int64_t)sms * 8);
     box_geometry_kernel<double><<<grid, 256, 0, c->stream>>>(c->d_gxyz, c->m, gp, bad_dev);
@@ -220,6 +230,8 @@ nb_status launch_box_geometry_pairs(const Mesh &m, double amp, const double *s, 
     for (int q = 0; q < m.n * m.n; q++) gp.D[q] = D[q];
     gp.amp = amp;
     gp.s[0] = s[0]; gp.s[1] = s[1]; gp.s[2] = s[2];
+    gp.ez0 = 0;
+    gp.ez_total = m.ez;
     const int sms = device_sms();
     const int grid = (int)(m.E < (int64_t)sms * 8 ? m.E : (int64_t)sms * 8);
     box_geometry_kernel<float2><<<grid, 256, 0, stream>>>(out, m, gp, bad_dev);

@@ -122,6 +122,10 @@ struct nb_ctx {
     int gxyz_exp = 1023;
     bool d_eo = false;          // D is centro-antisymmetric: even-odd line products
     bool is_box = false;        // built by nb_setup_box (coordinates known)
+    // slab of a z-partitioned box (nb_setup_slab): element layers
+    // slab_z0 .. slab_z0 + m.ez - 1 of a box slab_ez_global layers high
+    bool slab = false;
+    int slab_z0 = 0, slab_ez_global = 0;
     double box_amp = 0.0, box_s[3] = {0, 0, 0};        // biased exponent of max|gxyz| (pairs are scaled by 2^-(gxyz_exp-1023))
     // CG workspace
     double *d_r = nullptr, *d_p = nullptr, *d_w = nullptr, *d_x = nullptr;

@@ -99,6 +99,15 @@ _SIGS = {
     "nb_timing_enable": [_vp, ctypes.c_int],
     "nb_timing_read": [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
     "nb_fp32_rate": [_dp],
+    "nb_setup_slab": [ctypes.POINTER(_vp), nb_box, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                      ctypes.c_double, _vp, _vp],
+    "nb_slab_info": [_vp, ctypes.POINTER(ctypes.c_int64), _ip, _ip],
+    "nb_slab_top_partial": [_vp, _vp, _vp],
+    "nb_slab_add_bottom": [_vp, _vp, _vp],
+    "nb_slab_bottom_value": [_vp, _vp, _vp],
+    "nb_slab_set_top": [_vp, _vp, _vp],
+    "nb_slab_dot": [_vp, _vp, _vp, _dp],
+    "nb_axpby": [_vp, ctypes.c_double, _vp, ctypes.c_double, _vp],
 }
 
 
@@ -339,6 +348,55 @@ def nb_fp32_rate() -> float:
     v = ctypes.c_double(0.0)
     _check(load().nb_fp32_rate(ctypes.byref(v)), "nb_fp32_rate")
     return v.value
+
+
+# ------------------------------------------------------------------ slabs
+def nb_setup_slab(mesh, z0: int, z1: int, n: int, amp: float, s, stream=None):
+    lib = load()
+    ctx = _vp()
+    Sh, Sp = _host(s, np.float64)
+    _check(lib.nb_setup_slab(ctypes.byref(ctx), nb_box(*mesh), int(z0), int(z1), int(n), float(amp), Sp,
+                             _stream_handle(stream)), "nb_setup_slab")
+    return ctx
+
+
+def nb_slab_info(ctx):
+    """(plane_nodes, has_below, has_above)."""
+    npl, lo, hi = ctypes.c_int64(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().nb_slab_info(ctx, ctypes.byref(npl), ctypes.byref(lo), ctypes.byref(hi)), "nb_slab_info")
+    return npl.value, bool(lo.value), bool(hi.value)
+
+
+def nb_slab_top_partial(ctx, w, buf):
+    _check(load().nb_slab_top_partial(ctx, _ptr(w, "torch.float64"), _ptr(buf, "torch.float64")),
+           "nb_slab_top_partial")
+
+
+def nb_slab_add_bottom(ctx, w, buf):
+    _check(load().nb_slab_add_bottom(ctx, _ptr(w, "torch.float64"), _ptr(buf, "torch.float64")),
+           "nb_slab_add_bottom")
+
+
+def nb_slab_bottom_value(ctx, w, buf):
+    _check(load().nb_slab_bottom_value(ctx, _ptr(w, "torch.float64"), _ptr(buf, "torch.float64")),
+           "nb_slab_bottom_value")
+
+
+def nb_slab_set_top(ctx, w, buf):
+    _check(load().nb_slab_set_top(ctx, _ptr(w, "torch.float64"), _ptr(buf, "torch.float64")),
+           "nb_slab_set_top")
+
+
+def nb_slab_dot(ctx, a, b) -> float:
+    out = ctypes.c_double(0.0)
+    _check(load().nb_slab_dot(ctx, _ptr(a, "torch.float64"), _ptr(b, "torch.float64"), ctypes.byref(out)),
+           "nb_slab_dot")
+    return out.value
+
+
+def nb_axpby(ctx, alpha: float, x, beta: float, y):
+    _check(load().nb_axpby(ctx, float(alpha), _ptr(x, "torch.float64"), float(beta), _ptr(y, "torch.float64")),
+           "nb_axpby")
 
 
 # ------------------------------------------------------------------ engine
