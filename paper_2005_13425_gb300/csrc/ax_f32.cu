@@ -122,6 +122,8 @@ ax_f32_staged_kernel(AxF32Args a, CgScalars *err, const __grid_constant__ F32Mat
         }
     };
     int issued[2] = {0, 0}, waited[2] = {0, 0};
+    unsigned pf[f32_points_per_thread<N, T>()];
+    f32_point_masks<N, T>(pf);
     int64_t e = blockIdx.x;
     if (t == 0 && e < a.E) issue(e, 0);
     issued[0] = e < a.E ? 1 : 0;
@@ -144,7 +146,7 @@ ax_f32_staged_kernel(AxF32Args a, CgScalars *err, const __grid_constant__ F32Mat
         o.w = a.w + e * N3;
         int ex = 0, ey = 0, ez = 0;
         if (MODE == 1) element_coords(e, a.m, ex, ey, ez);
-        f32_element_staged<N, MODE, T>(smf + s * STAGE, smf + 2 * STAGE, o, beta, xa, ex, ey, ez, a.m, D, dot);
+        f32_element_staged<N, MODE, T>(smf + s * STAGE, smf + 2 * STAGE, o, beta, xa, ex, ey, ez, a.m, D, dot, pf);
     }
     if (!ok) {   // drain the copies in flight before leaving, then report
         if (t == 0) {

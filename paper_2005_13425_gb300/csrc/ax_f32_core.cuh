@@ -58,6 +58,80 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// One line product along a direction of compile-time stride S (1, N or
+// N^2): out[m S] = sum_l M(m,l) in[l S], M = D or (TR) D^T, accumulated as
+// M(m,0) x_0 followed by FMAs in l order.  A constant stride lets every
+// shared-memory access use an immediate offset (no address arithmetic per
+// access); along r (S = 1, even N) the line is read and written as float2,
+// which also removes the 2-way bank conflicts of 32 consecutive lines that
+// are N floats apart.
+template <int N, int S, bool TR>
+__device__ __forceinline__ void f32_line(const float *in, float *out, const F32Mat<N> &D) {
+    constexpr bool PAIRS = S == 1 && N % 2 == 0;
+    float x[N];
+    if constexpr (PAIRS) {
+        const float2 *in2 = reinterpret_cast<const float2 *>(in);
+#pragma unroll
+        for (int l = 0; l < N / 2; l++) {
+            const float2 v = in2[l];
+            x[2 * l] = v.x;
+            x[2 * l + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int l = 0; l < N; l++) x[l] = in[l * S];
+    }
+    auto dot_row = [&](int mm) {
+        float acc = (TR ? D.d[mm] : D.d[mm * N]) * x[0];
+#pragma unroll
+        for (int l = 1; l < N; l++) acc = fmaf(TR ? D.d[l * N + mm] : D.d[mm * N + l], x[l], acc);
+        return acc;
+    };
+    if constexpr (PAIRS) {
+        float2 *o2 = reinterpret_cast<float2 *>(out);
+#pragma unroll
+        for (int mm = 0; mm < N / 2; mm++) o2[mm] = make_float2(dot_row(2 * mm), dot_row(2 * mm + 1));
+    } else {
+#pragma unroll
+        for (int mm = 0; mm < N; mm++) out[mm * S] = dot_row(mm);
+    }
+}
+
+// The 3 N^2 line products of one pass, thread t taking tasks t, t + T, ...:
+// lines along r read i0 and write o0, along s i1 / o1, along t i2 / o2.
+template <int N, int T, bool TR>
+__device__ __forceinline__ void f32_line_pass(const float *i0, const float *i1, const float *i2, float *o0,
+                                              float *o1, float *o2, const F32Mat<N> &D) {
+    constexpr int N2 = N * N;
+    for (int task = threadIdx.x; task < 3 * N2; task += T) {
+        if (task < N2) {
+            f32_line<N, 1, TR>(i0 + N * task, o0 + N * task, D);
+        } else if (task < 2 * N2) {
+            const int c = task - N2;
+            const int base = c % N + N2 * (c / N);
+            f32_line<N, N, TR>(i1 + base, o1 + base, D);
+        } else {
+            const int c = task - 2 * N2;
+            f32_line<N, N2, TR>(i2 + c, o2 + c, D);
+        }
+    }
+}
+
+// Box-face masks (point_faces) of the points q = threadIdx.x + k T a thread
+// owns in the pointwise passes, computed once per kernel.
+template <int N, int T>
+__host__ __device__ constexpr int f32_points_per_thread() {
+    return (N * N * N + T - 1) / T;
+}
+template <int N, int T>
+__device__ __forceinline__ void f32_point_masks(unsigned *pf) {
+#pragma unroll
+    for (int k = 0; k < f32_points_per_thread<N, T>(); k++) {
+        const int q = threadIdx.x + k * T;
+        pf[k] = q < N * N * N ? point_faces<N>(q) : 0u;
+    }
+}
+
 // Per-element arguments of f32_element (pointers offset to the element).
 struct F32ElemIO {
     const float *u;   // MODE 0: input
@@ -109,21 +183,7 @@ __device__ __forceinline__ void f32_element(const F32ElemIO &io, float beta, flo
     }
     cp_async_commit();
     __syncthreads();
-    for (int task = t; task < 3 * N2; task += T) {
-        int stride;
-        const int base = f32_line_of<N>(task, stride);
-        float *Wd = task < N2 ? W0 : (task < 2 * N2 ? W1 : W2);
-        float x[N];
-#pragma unroll
-        for (int l = 0; l < N; l++) x[l] = U[base + l * stride];
-#pragma unroll
-        for (int mm = 0; mm < N; mm++) {
-            float acc = D.d[mm * N] * x[0];
-#pragma unroll
-            for (int l = 1; l < N; l++) acc = fmaf(D.d[mm * N + l], x[l], acc);
-            Wd[base + mm * stride] = acc;
-        }
-    }
+    f32_line_pass<N, T, false>(U, U, U, W0, W1, W2, D);
     cp_async_wait_all();
     __syncthreads();
     for (int q = t; q < N3; q += T) {
@@ -135,22 +195,7 @@ __device__ __forceinline__ void f32_element(const F32ElemIO &io, float beta, flo
         W2[q] = fmaf(g2, wr, fmaf(g4, ws, g5 * wt));
     }
     __syncthreads();
-    for (int task = t; task < 3 * N2; task += T) {
-        int stride;
-        const int base = f32_line_of<N>(task, stride);
-        const float *Ud = task < N2 ? W0 : (task < 2 * N2 ? W1 : W2);
-        float *Pd = task < N2 ? U : (task < 2 * N2 ? P1 : P2);
-        float x[N];
-#pragma unroll
-        for (int l = 0; l < N; l++) x[l] = Ud[base + l * stride];
-#pragma unroll
-        for (int mm = 0; mm < N; mm++) {
-            float acc = D.d[mm] * x[0];
-#pragma unroll
-            for (int l = 1; l < N; l++) acc = fmaf(D.d[l * N + mm], x[l], acc);
-            Pd[base + mm * stride] = acc;
-        }
-    }
+    f32_line_pass<N, T, true>(W0, W1, W2, U, P1, P2, D);
     __syncthreads();
     const unsigned bf = MODE == 1 ? box_faces(ex, ey, ez, m) : 0u;
     for (int q = t; q < N3; q += T) {
@@ -201,12 +246,13 @@ struct F32StagedOut {
     float *w;   // ax_e output
 };
 
-// Element body on stage `st` (whole CTA).  Ends with fence + barrier, after
-// which the stage may be refilled.
+// Element body on stage `st` (whole CTA).  pf: the thread's point-face
+// masks (f32_point_masks).  Ends with fence + barrier, after which the
+// stage may be refilled.
 template <int N, int MODE, int T>
 __device__ __forceinline__ void f32_element_staged(float *st, float *W, const F32StagedOut &o, float beta,
                                                    float xa, int ex, int ey, int ez, const Mesh &m,
-                                                   const F32Mat<N> &D, dfa::Acc32 &dot) {
+                                                   const F32Mat<N> &D, dfa::Acc32 &dot, const unsigned *pf) {
     constexpr int N2 = N * N, N3 = N * N * N;
     float *G = st;
     float *U = st + 6 * N3;                    // MODE 0: u; MODE 1: r then (below) p
@@ -232,21 +278,7 @@ __device__ __forceinline__ void f32_element_staged(float *st, float *W, const F3
         U = P;
         __syncthreads();
     }
-    for (int task = t; task < 3 * N2; task += T) {
-        int stride;
-        const int base = f32_line_of<N>(task, stride);
-        float *Wd = task < N2 ? W0 : (task < 2 * N2 ? W1 : W2);
-        float x[N];
-#pragma unroll
-        for (int l = 0; l < N; l++) x[l] = U[base + l * stride];
-#pragma unroll
-        for (int mm = 0; mm < N; mm++) {
-            float acc = D.d[mm * N] * x[0];
-#pragma unroll
-            for (int l = 1; l < N; l++) acc = fmaf(D.d[mm * N + l], x[l], acc);
-            Wd[base + mm * stride] = acc;
-        }
-    }
+    f32_line_pass<N, T, false>(U, U, U, W0, W1, W2, D);
     __syncthreads();
     for (int q = t; q < N3; q += T) {
         const float wr = W0[q], ws = W1[q], wt = W2[q];
@@ -258,28 +290,16 @@ __device__ __forceinline__ void f32_element_staged(float *st, float *W, const F3
     }
     __syncthreads();
     float *P0 = G, *P1 = G + N3, *P2 = G + 2 * N3;   // G is consumed
-    for (int task = t; task < 3 * N2; task += T) {
-        int stride;
-        const int base = f32_line_of<N>(task, stride);
-        const float *Ud = task < N2 ? W0 : (task < 2 * N2 ? W1 : W2);
-        float *Pd = task < N2 ? P0 : (task < 2 * N2 ? P1 : P2);
-        float x[N];
-#pragma unroll
-        for (int l = 0; l < N; l++) x[l] = Ud[base + l * stride];
-#pragma unroll
-        for (int mm = 0; mm < N; mm++) {
-            float acc = D.d[mm] * x[0];
-#pragma unroll
-            for (int l = 1; l < N; l++) acc = fmaf(D.d[l * N + mm], x[l], acc);
-            Pd[base + mm * stride] = acc;
-        }
-    }
+    f32_line_pass<N, T, true>(W0, W1, W2, P0, P1, P2, D);
     __syncthreads();
     const unsigned bf = MODE == 1 ? box_faces(ex, ey, ez, m) : 0u;
-    for (int q = t; q < N3; q += T) {
+#pragma unroll
+    for (int k = 0; k < f32_points_per_thread<N, T>(); k++) {
+        const int q = t + k * T;
+        if (f32_points_per_thread<N, T>() * T != N3 && q >= N3) break;
         float wv = P0[q] + P1[q] + P2[q];
         if (MODE == 1) {
-            if (point_faces<N>(q) & bf)
+            if (pf[k] & bf)
                 wv = 0.f;
             else
                 dot.add_prod(wv, U[q]);

@@ -485,6 +485,8 @@ eng_m_head_staged(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, c
     };
     int issued[2] = {1, 0}, waited[2] = {0, 0};
     if (t == 0) issue(cur, 0);
+    unsigned pf[f32_points_per_thread<N, T>()];
+    f32_point_masks<N, T>(pf);
     dfa::Acc32 dot;
     bool ok = true;
     for (int i = 0;; i++) {
@@ -508,7 +510,7 @@ eng_m_head_staged(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, c
         o.w = P.w32 + cur.e * N3;
         int ex, ey, ez;
         element_coords(cur.e, P.m, ex, ey, ez);
-        f32_element_staged<N, 1, T>(smf + s * STAGE, smf + 2 * STAGE, o, beta, xa, ex, ey, ez, P.m, D, dot);
+        f32_element_staged<N, 1, T>(smf + s * STAGE, smf + 2 * STAGE, o, beta, xa, ex, ey, ez, P.m, D, dot, pf);
         if (cur.e + 1 == cur.e1) {   // the tile is complete
             const double b = block_sum(dot.value(), red);
             dot = dfa::Acc32();
