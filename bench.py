@@ -484,6 +484,32 @@ def run_gpu(args, rank, world, local):
         finally:
             nekgb.nb_destroy(cs)
 
+    # ---- the partitioned box on one GPU: two slabs of 8 element layers,
+    # the host-driven partitioned CG (interface exchanges as device copies)
+    from paper_2005_13425_gb300 import partition
+    slabs = [partition.GpuSlab(nekgb, DIMS, z0, z1, NGLL, inputs.PERTURB_AMP, s, stream)
+             for z0, z1 in partition.slab_bounds(DIMS[2], 2)]
+    try:
+        pbox = partition.PartitionedBox(slabs, partition.Exchange(2, 0, 2))
+        layer = DIMS[0] * DIMS[1]
+        fs = [f[z0 * layer:z1 * layer].contiguous() for z0, z1 in partition.slab_bounds(DIMS[2], 2)]
+        xs = [sl.new_field() for sl in slabs]
+        pbox.cg(fs, xs, tol=0.0, maxit=3)
+        for xx in xs:
+            xx.zero_()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        pbox.cg(fs, xs, tol=0.0, maxit=20)
+        p1.record(stream)
+        p1.synchronize()
+        pit = p0.elapsed_time(p1) / 20
+        partitioned = {"slabs": 2, "ms_per_iteration": pit, "gdofs": D / (pit * 1e-3) / 1e9,
+                       "note": "host-driven partitioned CG (two exchanges of 168 KB planes and two "
+                               "scalar reductions per iteration, no CUDA graph), both slabs on one GPU"}
+    finally:
+        for sl in slabs:
+            sl.close()
+
     # ---- config 1: 4x4x4 elements, n = 8, 100 fixed CG iterations (the
     # paper's run length), median of 20 solves
     c1 = nekgb.nb_setup_box((4, 4, 4), 8, inputs.PERTURB_AMP, s, nekgb.NB_FP64, stream)
@@ -578,6 +604,7 @@ def run_gpu(args, rank, world, local):
         "ax_dssum": {"ms": t_axds, "gdofs": D / (t_axds * 1e-3) / 1e9},
         "ax_sweep_n10": sweep,
         "config1_4x4x4_n8_cg100": config1,
+        "partitioned_2slabs_one_gpu": partitioned,
         "ax_only_native_fp64": {"ms": t_ax_fp64, "gdofs": D / (t_ax_fp64 * 1e-3) / 1e9,
                                 "fp64_tflops": metrics.ax_flops_per_point(NGLL) * D / (t_ax_fp64 * 1e-3) / 1e12},
         "e2e": {"value": value_e2e, "unit": "GDOF/s",
@@ -627,7 +654,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-vs-FP64 solves")
     ap.add_argument("--no-engine", action="store_true", help="skip the batched and served solves")
-    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-requests", type=int, default=64)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -2,8 +2,11 @@
 
 Tolerances (derived from the arithmetic):
 * ax_e, apply: max-norm relative error <= 1e-12 (FP64 contract) on identical
-  inputs (the same D and gxyz on both sides), at every n; the absolute form
-  1e-12 |D|^2 |G| |u| only for the near-null input A 1.
+  inputs (the same D and gxyz on both sides), at every n, for data whose
+  output is of the order of its terms (random u); for smooth data, whose
+  output cancels 1e3-2e4 times, 1e-12 |w| + 2^-50 |D|^2 |G| |u| (48-bit
+  double-float arithmetic); the absolute form 1e-12 |D|^2 |G| |u| for the
+  near-null input A 1.
 * device-built geometry against the oracle's: n eps kappa_J of max|G|, with
   kappa_J = |D|_inf max|x| / min|dx/dr| the condition number of the
   isoparametric Jacobian J = D x (absolute coordinates: two FP64
@@ -134,6 +137,31 @@ def test_ax_general_derivative_matrix(nek, oracle, n):
             w = torch.empty(P["E"], n ** 3, dtype=torch.float64, device="cuda")
             nek.nb_ax(ctx, dev(u), w)
             assert rel_err(host(w), want) <= AX_TOL, variant
+
+
+@pytest.mark.parametrize("n", [8, 10, 12])
+def test_ax_smooth_input_error_bound(nek, oracle, n):
+    """Smooth data (the manufactured solution sin(pi x) sin(pi y) sin(pi z)
+    and sin(3x) cos(2y) + 0.3 z^2) cancel 3.5e3 to 1.9e4 times between the
+    terms of ax_e and its output.  The double-float kernel carries 48-bit
+    significands, so its error there is set by the term scale TS =
+    |D|_inf^2 |G| |u| (emulated: about 2^-53 TS), and the bound is
+    1e-12 |w| + 2^-50 TS: the relative contract where the output is of the
+    order of its terms, 2^-50 of the terms where it is not."""
+    dims = (4, 4, 4)
+    P = oracle_problem(oracle, dims, n)
+    X = P["xyz"]
+    fields = [np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1]) * np.sin(np.pi * X[:, 2]),
+              np.sin(3.0 * X[:, 0]) * np.cos(2.0 * X[:, 1]) + 0.3 * X[:, 2] ** 2]
+    with Ctx(nek, dims, n, P["D"], P["gxyz"]) as ctx:
+        for u in fields:
+            want = oracle.ax_e(P["D"], P["gxyz"], u)
+            w = torch.empty(P["E"], n ** 3, dtype=torch.float64, device="cuda")
+            nek.nb_ax(ctx, dev(u), w)
+            got = host(w)
+            TS = np.abs(P["D"]).sum(1).max() ** 2 * np.abs(P["gxyz"]).max() * np.abs(u).max()
+            assert TS / np.abs(want).max() > 1e3            # the inputs are the high-cancellation case
+            assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max() + 2.0 ** -50 * TS
 
 
 def test_ax_ragged_many_elements(nek, oracle):
