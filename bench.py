@@ -341,6 +341,28 @@ def mixed_vs_fp64(nekgb, stream, n, tol=1e-10):
     return out
 
 
+# ---------------------------------------------------------------- serving
+def serving(nekgb, stream, count, capacity_gdofs=None):
+    """Config 5: Poisson arrivals at 0.5, 0.95 and 2 x the FP64 batched
+    capacity (measured here when not given), FP64 and mixed requests."""
+    from paper_2005_13425_gb300 import workloads
+    if capacity_gdofs is None:
+        capacity_gdofs = workloads.batched_run(nekgb, stream, workloads.batch_list(256, seed=4), iters=100,
+                                               sequential=False)["gdofs"]
+    reqs = workloads.serving_requests(count, seed=5)
+    arena = 48 << 30
+    its = workloads.measure_iterations(nekgb, stream, reqs, arena)
+    out = []
+    for u in (0.5, 0.95, 2.0):
+        for prec in (nekgb.NB_FP64, nekgb.NB_MIXED):
+            srv = workloads.serving_run(nekgb, stream, reqs, u, capacity_gdofs * 1e9, its, arena, prec=prec)
+            srv["config"] = (f"{len(reqs)} requests, Poisson arrivals at {u} x the FP64 batched capacity, "
+                             "E log-uniform in [64, 32768], n from {6, 8, 10, 12}, tol 1e-8 or 1e-10, "
+                             "48 GiB arena")
+            out.append(srv)
+    return out
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_gpu(args, rank, world, local):
     import torch
@@ -354,6 +376,12 @@ def run_gpu(args, rank, world, local):
     nekgb.load()
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
+    if args.serving_study:
+        out = {"serving_study": serving(nekgb, stream, args.serve_requests)}
+        if rank == 0:
+            print(json.dumps(out))
+        dist.close()
+        return 0
     E = DIMS[0] * DIMS[1] * DIMS[2]
     D = E * NGLL ** 3
     s = inputs.perturbation_coeffs(inputs.SEED_MESH)
@@ -624,18 +652,7 @@ def run_gpu(args, rank, world, local):
                                                       prec=nekgb.NB_MIXED)
         line["batched_mixed"]["config"] = ("the same 256 problems, mixed precision (FP32 inner CG, FP64 "
                                            "defect correction), 100 inner iterations")
-        reqs = workloads.serving_requests(args.serve_requests, seed=5)
-        arena = 48 << 30
-        its = workloads.measure_iterations(nekgb, stream, reqs, arena)
-        cap = line["batched"]["gdofs"] * 1e9
-        line["serving"] = []
-        for u in (0.5, 0.95, 2.0):
-            for prec in (nekgb.NB_FP64, nekgb.NB_MIXED):
-                srv = workloads.serving_run(nekgb, stream, reqs, u, cap, its, arena, prec=prec)
-                srv["config"] = (f"{len(reqs)} requests, Poisson arrivals at {u} x the FP64 batched capacity, "
-                                 "E log-uniform in [64, 32768], n from {6, 8, 10, 12}, tol 1e-8 or 1e-10, "
-                                 "48 GiB arena")
-                line["serving"].append(srv)
+        line["serving"] = serving(nekgb, stream, args.serve_requests, line["batched"]["gdofs"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     nekgb.nb_destroy(ctx)
@@ -655,6 +672,8 @@ def main(argv=None):
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-vs-FP64 solves")
     ap.add_argument("--no-engine", action="store_true", help="skip the batched and served solves")
     ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serving-study", action="store_true",
+                    help="run only the served workload (config 5) and print its records")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -209,15 +209,29 @@ __device__ __forceinline__ void line_eo_s(const float2 *in, float2 *out, const E
 
 // The 3 N^2 even-odd line products of one pass, thread t taking tasks t,
 // t + T, ...: lines along r read i0 and write o0, along s i1 / o1, along t
-// i2 / o2 (task order and line geometry as line_of).
+// i2 / o2 (task order and line geometry as line_of).  A warp whose 32 tasks
+// lie in one direction takes that direction's constant-stride body; a warp
+// that straddles two directions (N^2 is rarely a multiple of 32) takes the
+// runtime-stride body for all its lanes, so no warp runs two bodies one
+// after the other.
 template <int N, int T>
 __device__ __forceinline__ void line_eo_pass(const float2 *i0, const float2 *i1, const float2 *i2, float2 *o0,
                                              float2 *o1, float2 *o2, const EoMat<N> &M) {
     constexpr int N2 = N * N;
+    static_assert(T % 32 == 0, "warp-aligned task groups");
     for (int task = threadIdx.x; task < 3 * N2; task += T) {
-        if (task < N2) {
+        const int first = task & ~31;
+        const int last = first + 31 < 3 * N2 - 1 ? first + 31 : 3 * N2 - 1;
+        const int d = first / N2;
+        if (d != last / N2) {                    // warp-uniform
+            int stride;
+            const int base = line_of<N>(task, stride);
+            const float2 *in = task < N2 ? i0 : (task < 2 * N2 ? i1 : i2);
+            float2 *out = task < N2 ? o0 : (task < 2 * N2 ? o1 : o2);
+            line_eo<N>(in, out, base, stride, M);
+        } else if (d == 0) {
             line_eo_s<N, 1>(i0 + N * task, o0 + N * task, M);
-        } else if (task < 2 * N2) {
+        } else if (d == 1) {
             const int c = task - N2;
             const int base = c % N + N2 * (c / N);
             line_eo_s<N, N>(i1 + base, o1 + base, M);

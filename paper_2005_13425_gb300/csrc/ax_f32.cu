@@ -81,7 +81,7 @@ ax_f32_kernel(AxF32Args a, const __grid_constant__ F32Mat<N> D) {
 // tests) each CTA's first wait is made on a barrier that nothing arrives on,
 // with that limit: it runs out, and the same drain-and-report path runs.
 template <int N, int MODE>
-__global__ void __launch_bounds__(ax_f32_threads(N))
+__global__ void __launch_bounds__(ax_f32_threads(N), f32_staged_min_blocks<N>())
 ax_f32_staged_kernel(AxF32Args a, CgScalars *err, const __grid_constant__ F32Mat<N> D) {
     constexpr int N3 = N * N * N;
     constexpr int T = ax_f32_threads(N);
@@ -105,20 +105,20 @@ ax_f32_staged_kernel(AxF32Args a, CgScalars *err, const __grid_constant__ F32Mat
     }
     __syncthreads();
     const bool with_x = MODE == 1 && xa != 0.f;
-    const unsigned bytes = 4u * (MODE == 1 ? (with_x ? 9 : 8) : 7) * N3;
-    // the geometric factors and x are read once per iteration: evict them
-    // first, so p and w stay in L2 for the dssum and update kernels
+    const unsigned bytes = 4u * (MODE == 1 ? (with_x ? 3 : 2) : 1) * N3;
+    // x is read once per iteration: evict it first, so p and w stay in L2
+    // for the update kernel (the geometric factors are streamed into
+    // registers with evict-first loads by the element body)
     const uint64_t stream_pol = t == 0 ? l2_evict_first_policy() : 0ull;
     auto issue = [&](int64_t e, int s) {   // thread 0
         float *st = smf + s * STAGE;
         mbar_expect_tx(&bars[s], bytes);
-        bulk_g2s_hint(st, a.g + e * 6 * N3, 4u * 6 * N3, &bars[s], stream_pol);
         if (MODE == 1) {
-            bulk_g2s(st + 6 * N3, a.r + e * N3, 4u * N3, &bars[s]);
-            bulk_g2s(st + 7 * N3, a.p + e * N3, 4u * N3, &bars[s]);
-            if (with_x) bulk_g2s_hint(st + 8 * N3, a.x + e * N3, 4u * N3, &bars[s], stream_pol);
+            bulk_g2s(st, a.r + e * N3, 4u * N3, &bars[s]);
+            bulk_g2s(st + N3, a.p + e * N3, 4u * N3, &bars[s]);
+            if (with_x) bulk_g2s_hint(st + 2 * N3, a.x + e * N3, 4u * N3, &bars[s], stream_pol);
         } else {
-            bulk_g2s(st + 6 * N3, a.u + e * N3, 4u * N3, &bars[s]);
+            bulk_g2s(st, a.u + e * N3, 4u * N3, &bars[s]);
         }
     };
     int issued[2] = {0, 0}, waited[2] = {0, 0};
@@ -146,7 +146,8 @@ ax_f32_staged_kernel(AxF32Args a, CgScalars *err, const __grid_constant__ F32Mat
         o.w = a.w + e * N3;
         int ex = 0, ey = 0, ez = 0;
         if (MODE == 1) element_coords(e, a.m, ex, ey, ez);
-        f32_element_staged<N, MODE, T>(smf + s * STAGE, smf + 2 * STAGE, o, beta, xa, ex, ey, ez, a.m, D, dot, pf);
+        f32_element_staged<N, MODE, T>(smf + s * STAGE, smf + 2 * STAGE, a.g + e * 6 * N3, o, beta, xa, ex, ey,
+                                       ez, a.m, D, dot, pf);
     }
     if (!ok) {   // drain the copies in flight before leaving, then report
         if (t == 0) {

@@ -97,14 +97,42 @@ __device__ __forceinline__ void f32_line(const float *in, float *out, const F32M
     }
 }
 
+// The same line product with a runtime stride, for warps whose lines run
+// in two directions.
+template <int N, bool TR>
+__device__ __forceinline__ void f32_line_rt(const float *in, float *out, int stride, const F32Mat<N> &D) {
+    float x[N];
+#pragma unroll
+    for (int l = 0; l < N; l++) x[l] = in[l * stride];
+#pragma unroll
+    for (int mm = 0; mm < N; mm++) {
+        float acc = (TR ? D.d[mm] : D.d[mm * N]) * x[0];
+#pragma unroll
+        for (int l = 1; l < N; l++) acc = fmaf(TR ? D.d[l * N + mm] : D.d[mm * N + l], x[l], acc);
+        out[mm * stride] = acc;
+    }
+}
+
 // The 3 N^2 line products of one pass, thread t taking tasks t, t + T, ...:
-// lines along r read i0 and write o0, along s i1 / o1, along t i2 / o2.
+// lines along r read i0 and write o0, along s i1 / o1, along t i2 / o2.  A
+// warp whose 32 tasks lie in one direction takes that direction's
+// constant-stride body; a warp that straddles two directions takes the
+// runtime-stride body for all its lanes (no warp runs two bodies serially).
 template <int N, int T, bool TR>
 __device__ __forceinline__ void f32_line_pass(const float *i0, const float *i1, const float *i2, float *o0,
                                               float *o1, float *o2, const F32Mat<N> &D) {
     constexpr int N2 = N * N;
+    static_assert(T % 32 == 0, "warp-aligned task groups");
     for (int task = threadIdx.x; task < 3 * N2; task += T) {
-        if (task < N2) {
+        const int first = task & ~31;
+        const int last = first + 31 < 3 * N2 - 1 ? first + 31 : 3 * N2 - 1;
+        if (first / N2 != last / N2) {           // warp-uniform
+            int stride;
+            const int base = f32_line_of<N>(task, stride);
+            const float *in = task < N2 ? i0 : (task < 2 * N2 ? i1 : i2);
+            float *out = task < N2 ? o0 : (task < 2 * N2 ? o1 : o2);
+            f32_line_rt<N, TR>(in + base, out + base, stride, D);
+        } else if (task < N2) {
             f32_line<N, 1, TR>(i0 + N * task, o0 + N * task, D);
         } else if (task < 2 * N2) {
             const int c = task - N2;
@@ -223,17 +251,31 @@ __device__ __forceinline__ void f32_element(const F32ElemIO &io, float beta, flo
 // shared memory fits nine CTAs per SM instead of five; the single-problem
 // solve measured faster staged at n = 8 as well (51.5 vs 54.0 ms).
 //
-// Shared memory (floats): stage s at s*f32_stage_floats: G [6n^3] then the
-// vectors (MODE 1: r, p, z; MODE 0: u); after both stages, W0..W2 [3n^3].
-// The backward partials reuse the current stage's G (consumed by then).
+// Shared memory (floats): stage s at s*f32_stage_floats holds the element's
+// vectors (MODE 1: r, p, z; MODE 0: u); after both stages, W0..W2 [3n^3]
+// (forward derivatives, then their geometric contraction) and the three
+// backward partials [3n^3].  The geometric factors do not pass through
+// shared memory: each thread loads its own points' six factors into
+// registers at the start of the element (streaming loads, coalesced), and
+// they arrive while the update and forward passes run.  That keeps a CTA at
+// 12 n^3 floats (48 KB at n = 10), four CTAs per SM instead of two.
 template <int N, int MODE>
 __host__ __device__ constexpr int f32_stage_floats() {
-    return (MODE == 1 ? 9 : 7) * N * N * N;
+    return (MODE == 1 ? 3 : 1) * N * N * N;
 }
 template <int N, int MODE>
 __host__ __device__ constexpr int f32_staged_smem_floats() {
-    return 2 * f32_stage_floats<N, MODE>() + 3 * N * N * N;
+    return 2 * f32_stage_floats<N, MODE>() + 6 * N * N * N;
 }
+// CTAs per SM the staged kernels ask the register allocator to allow:
+// as many as the shared memory holds (228 KB, 1 KB reserved per CTA), at
+// most four.
+template <int N>
+__host__ __device__ constexpr int f32_staged_min_blocks() {
+    constexpr int by_smem = (228 * 1024) / (4 * f32_staged_smem_floats<N, 1>() + 1024);
+    return by_smem < 4 ? (by_smem < 1 ? 1 : by_smem) : 4;
+}
+
 template <int N>
 __host__ __device__ constexpr bool f32_staged_ok() {
     return (N % 2 == 0) && N <= 10;
@@ -246,20 +288,36 @@ struct F32StagedOut {
     float *w;   // ax_e output
 };
 
-// Element body on stage `st` (whole CTA).  pf: the thread's point-face
-// masks (f32_point_masks).  Ends with fence + barrier, after which the
-// stage may be refilled.
+// Element body on stage `st` (whole CTA); g: the element's geometric
+// factors [6][n^3] in global memory.  pf: the thread's point-face masks
+// (f32_point_masks).  Ends with fence + barrier, after which the stage may
+// be refilled.
 template <int N, int MODE, int T>
-__device__ __forceinline__ void f32_element_staged(float *st, float *W, const F32StagedOut &o, float beta,
-                                                   float xa, int ex, int ey, int ez, const Mesh &m,
-                                                   const F32Mat<N> &D, dfa::Acc32 &dot, const unsigned *pf) {
-    constexpr int N2 = N * N, N3 = N * N * N;
-    float *G = st;
-    float *U = st + 6 * N3;                    // MODE 0: u; MODE 1: r then (below) p
+__device__ __forceinline__ void f32_element_staged(float *st, float *W, const float *__restrict__ g,
+                                                   const F32StagedOut &o, float beta, float xa, int ex, int ey,
+                                                   int ez, const Mesh &m, const F32Mat<N> &D, dfa::Acc32 &dot,
+                                                   const unsigned *pf) {
+    constexpr int N3 = N * N * N;
+    constexpr int PPT = f32_points_per_thread<N, T>();
+    constexpr bool RAGGED = PPT * T != N3;
+    float *U = st;                             // MODE 0: u; MODE 1: r then (below) p
     float *W0 = W, *W1 = W + N3, *W2 = W + 2 * N3;
+    float *P0 = W + 3 * N3, *P1 = W + 4 * N3, *P2 = W + 5 * N3;
     const int t = threadIdx.x;
+    float gv[PPT][6];
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        const int q = t + k * T;
+        if (!RAGGED || q < N3) {
+#pragma unroll
+            for (int c = 0; c < 6; c++) gv[k][c] = __ldcs(g + c * N3 + q);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 6; c++) gv[k][c] = 0.f;
+        }
+    }
     if (MODE == 1) {
-        float *R = st + 6 * N3, *P = st + 7 * N3, *Z = st + 8 * N3;
+        float *R = st, *P = st + N3, *Z = st + 2 * N3;
         if (xa != 0.f) {
             for (int q = t; q < N3; q += T) {
                 const float pold = P[q];
@@ -280,23 +338,23 @@ __device__ __forceinline__ void f32_element_staged(float *st, float *W, const F3
     }
     f32_line_pass<N, T, false>(U, U, U, W0, W1, W2, D);
     __syncthreads();
-    for (int q = t; q < N3; q += T) {
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        const int q = t + k * T;
+        if (RAGGED && q >= N3) break;
         const float wr = W0[q], ws = W1[q], wt = W2[q];
-        const float g0 = G[q], g1 = G[N3 + q], g2 = G[2 * N3 + q];
-        const float g3 = G[3 * N3 + q], g4 = G[4 * N3 + q], g5 = G[5 * N3 + q];
-        W0[q] = fmaf(g0, wr, fmaf(g1, ws, g2 * wt));
-        W1[q] = fmaf(g1, wr, fmaf(g3, ws, g4 * wt));
-        W2[q] = fmaf(g2, wr, fmaf(g4, ws, g5 * wt));
+        W0[q] = fmaf(gv[k][0], wr, fmaf(gv[k][1], ws, gv[k][2] * wt));
+        W1[q] = fmaf(gv[k][1], wr, fmaf(gv[k][3], ws, gv[k][4] * wt));
+        W2[q] = fmaf(gv[k][2], wr, fmaf(gv[k][4], ws, gv[k][5] * wt));
     }
     __syncthreads();
-    float *P0 = G, *P1 = G + N3, *P2 = G + 2 * N3;   // G is consumed
     f32_line_pass<N, T, true>(W0, W1, W2, P0, P1, P2, D);
     __syncthreads();
     const unsigned bf = MODE == 1 ? box_faces(ex, ey, ez, m) : 0u;
 #pragma unroll
-    for (int k = 0; k < f32_points_per_thread<N, T>(); k++) {
+    for (int k = 0; k < PPT; k++) {
         const int q = t + k * T;
-        if (f32_points_per_thread<N, T>() * T != N3 && q >= N3) break;
+        if (RAGGED && q >= N3) break;
         float wv = P0[q] + P1[q] + P2[q];
         if (MODE == 1) {
             if (pf[k] & bf)

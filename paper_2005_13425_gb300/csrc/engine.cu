@@ -507,14 +507,14 @@ eng_m_head(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const in
 
 // The inner head with bulk-copy staging (f32_element_staged): each CTA walks
 // its work items -- the elements of its active tiles, in order -- and
-// while it computes one, the copy engine brings the next one's geometric
-// factors and r, p, z slabs into the other stage, across tile and problem
-// boundaries.  A tile's last element closes the tile's <w,p> partial; a
+// while it computes one, the copy engine brings the next one's r, p, z
+// slabs into the other stage, across tile and problem boundaries (the
+// geometric factors go straight to registers).  A tile's last element closes the tile's <w,p> partial; a
 // problem's last tile forms alpha.  A copy that does not complete within
 // ~1 s ends the CTA after draining its copies and marks the problem it was
 // on with NB_ERR_TIMEOUT.  Even n <= 10 (16-byte aligned slabs).
 template <int N, int T>
-__global__ void __launch_bounds__(T)
+__global__ void __launch_bounds__(T, f32_staged_min_blocks<N>())
 eng_m_head_staged(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles,
                   const __grid_constant__ F32Mat<N> D) {
     constexpr int N3 = N * N * N;
@@ -564,11 +564,10 @@ eng_m_head_staged(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, c
         const ProbDesc &P = desc[tiles[it.ti].x];
         const bool wx = (float)P.si.x_alpha != 0.f;
         float *st = smf + s * STAGE;
-        mbar_expect_tx(&bars[s], 4u * (wx ? 9 : 8) * N3);
-        bulk_g2s_hint(st, P.g32 + it.e * 6 * N3, 4u * 6 * N3, &bars[s], pol);
-        bulk_g2s(st + 6 * N3, P.r32 + it.e * N3, 4u * N3, &bars[s]);
-        bulk_g2s(st + 7 * N3, P.p32 + it.e * N3, 4u * N3, &bars[s]);
-        if (wx) bulk_g2s_hint(st + 8 * N3, P.z32 + it.e * N3, 4u * N3, &bars[s], pol);
+        mbar_expect_tx(&bars[s], 4u * (wx ? 3 : 2) * N3);
+        bulk_g2s(st, P.r32 + it.e * N3, 4u * N3, &bars[s]);
+        bulk_g2s(st + N3, P.p32 + it.e * N3, 4u * N3, &bars[s]);
+        if (wx) bulk_g2s_hint(st + 2 * N3, P.z32 + it.e * N3, 4u * N3, &bars[s], pol);
     };
     int issued[2] = {1, 0}, waited[2] = {0, 0};
     if (t == 0) issue(cur, 0);
@@ -597,7 +596,8 @@ eng_m_head_staged(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, c
         o.w = P.w32 + cur.e * N3;
         int ex, ey, ez;
         element_coords(cur.e, P.m, ex, ey, ez);
-        f32_element_staged<N, 1, T>(smf + s * STAGE, smf + 2 * STAGE, o, beta, xa, ex, ey, ez, P.m, D, dot, pf);
+        f32_element_staged<N, 1, T>(smf + s * STAGE, smf + 2 * STAGE, P.g32 + cur.e * 6 * N3, o, beta, xa, ex, ey,
+                                    ez, P.m, D, dot, pf);
         if (cur.e + 1 == cur.e1) {   // the tile is complete
             const double b = block_sum(dot.value(), red);
             dot = dfa::Acc32();
