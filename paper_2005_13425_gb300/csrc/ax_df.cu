@@ -172,8 +172,6 @@ __device__ __forceinline__ u128 cg_head_pipelined(const AxDfArgs &a, double beta
             }
         }
     };
-    unsigned pf[df_points_per_thread<N, T>()];   // box-face masks of this thread's points
-    df_point_masks<N, T>(pf);
     u128 acc = 0;
     int64_t e = blockIdx.x;
     if (e < a.E) stage(e, S0);
@@ -185,15 +183,14 @@ __device__ __forceinline__ u128 cg_head_pipelined(const AxDfArgs &a, double beta
         float2 *X = odd ? S1 : S0;
         float2 *F0 = odd ? S0 : S1;
         // forward: wr, ws, wt along this thread's line
-        if constexpr (EO) {
-            line_eo_pass<N, T>(X, X, X, F0, S2, S3, D.fwd);
-        } else {
-            for (int task = t; task < 3 * N2; task += T) {
-                int stride;
-                const int base = line_of<N>(task, stride);
-                float2 *Fd = task < N2 ? F0 : (task < 2 * N2 ? S2 : S3);
+        for (int task = t; task < 3 * N2; task += T) {
+            int stride;
+            const int base = line_of<N>(task, stride);
+            float2 *Fd = task < N2 ? F0 : (task < 2 * N2 ? S2 : S3);
+            if constexpr (EO)
+                line_eo<N>(X, Fd, base, stride, D.fwd);
+            else
                 line_plain<N, false>(X, Fd, base, stride, D);
-            }
         }
         __syncthreads();
         // geometric contraction, pointwise, in place
@@ -217,16 +214,15 @@ __device__ __forceinline__ u128 cg_head_pipelined(const AxDfArgs &a, double beta
         }
         __syncthreads();
         // backward: the three partials of w, into X (consumed), S4, S5
-        if constexpr (EO) {
-            line_eo_pass<N, T>(F0, S2, S3, X, S4, S5, D.bwd);
-        } else {
-            for (int task = t; task < 3 * N2; task += T) {
-                int stride;
-                const int base = line_of<N>(task, stride);
-                const float2 *Fd = task < N2 ? F0 : (task < 2 * N2 ? S2 : S3);
-                float2 *Pd = task < N2 ? X : (task < 2 * N2 ? S4 : S5);
+        for (int task = t; task < 3 * N2; task += T) {
+            int stride;
+            const int base = line_of<N>(task, stride);
+            const float2 *Fd = task < N2 ? F0 : (task < 2 * N2 ? S2 : S3);
+            float2 *Pd = task < N2 ? X : (task < 2 * N2 ? S4 : S5);
+            if constexpr (EO)
+                line_eo<N>(Fd, Pd, base, stride, D.bwd);
+            else
                 line_plain<N, true>(Fd, Pd, base, stride, D);
-            }
         }
         if (t == 0) s_next = (long long)gridDim.x + (long long)nxt;
         __syncthreads();
@@ -247,7 +243,7 @@ __device__ __forceinline__ u128 cg_head_pipelined(const AxDfArgs &a, double beta
                 if (df_points_per_thread<N, T>() * T != N3 && q >= N3) break;
                 const float2 s = dfa::add(dfa::add(X[q], S4[q]), S5[q]);
                 double wv = dfa::join_scaled(s, sh_out);
-                if (pf[kk] & bf)
+                if (point_faces<N>(q) & bf)
                     wv = 0.0;
                 else
                     de = fma(wv, p[q], de);

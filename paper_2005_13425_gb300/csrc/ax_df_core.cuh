@@ -150,98 +150,6 @@ __device__ __forceinline__ void line_eo(const float2 *in, float2 *out, int base,
     }
 }
 
-// line_eo with a compile-time stride S (1, N or N^2) and `in`, `out`
-// already offset to the line: every shared-memory access takes an
-// immediate offset, and along r (S = 1, even N) the line is read two pairs
-// at a time (float4; 16-byte aligned because the line starts at an even
-// pair index), which also avoids the bank conflicts of 8-byte accesses to
-// lines N pairs apart.  The arithmetic is line_eo's, in the same order.
-template <int N, int S>
-__device__ __forceinline__ void line_eo_s(const float2 *in, float2 *out, const EoMat<N> &M) {
-    constexpr int H = N / 2;
-    float2 x[N];
-    if constexpr (S == 1 && N % 2 == 0) {
-        const float4 *in4 = reinterpret_cast<const float4 *>(in);
-#pragma unroll
-        for (int l = 0; l < N / 2; l++) {
-            const float4 v = in4[l];
-            x[2 * l] = make_float2(v.x, v.y);
-            x[2 * l + 1] = make_float2(v.z, v.w);
-        }
-    } else {
-#pragma unroll
-        for (int l = 0; l < N; l++) x[l] = in[l * S];
-    }
-    float sh[H], sl[H], dh[H], dl[H];
-#pragma unroll
-    for (int l = 0; l < H; l++) {
-        const float2 a = x[l], b = x[N - 1 - l];
-        const float2 s = dfa::add(a, b);
-        const float2 d = dfa::add(a, make_float2(-b.x, -b.y));
-        sh[l] = s.x; sl[l] = s.y;
-        dh[l] = d.x; dl[l] = d.y;
-    }
-    float ch = 0.f, cl = 0.f;
-    if (N & 1) {
-        ch = x[H].x;
-        cl = x[H].y;
-    }
-#pragma unroll
-    for (int m = 0; m < H; m++) {
-        dfa::Acc P = dfa::first(M.ah[m * H], M.al[m * H], dh[0], dl[0]);
-#pragma unroll
-        for (int l = 1; l < H; l++) dfa::fma(P, M.ah[m * H + l], M.al[m * H + l], dh[l], dl[l]);
-        dfa::Acc Q = dfa::first(M.bh[m * (H + 1)], M.bl[m * (H + 1)], sh[0], sl[0]);
-#pragma unroll
-        for (int l = 1; l < H; l++) dfa::fma(Q, M.bh[m * (H + 1) + l], M.bl[m * (H + 1) + l], sh[l], sl[l]);
-        if (N & 1) dfa::fma(Q, M.bh[m * (H + 1) + H], M.bl[m * (H + 1) + H], ch, cl);
-        out[m * S] = dfa::add_acc(P, Q, 1.f);
-        out[(N - 1 - m) * S] = dfa::add_acc(P, Q, -1.f);
-    }
-    if (N & 1) {
-        dfa::Acc Y = dfa::first(M.ch[0], M.cl[0], dh[0], dl[0]);
-#pragma unroll
-        for (int l = 1; l < H; l++) dfa::fma(Y, M.ch[l], M.cl[l], dh[l], dl[l]);
-        dfa::fma(Y, M.ch[H], M.cl[H], ch, cl);
-        out[H * S] = dfa::norm(Y);
-    }
-}
-
-// The 3 N^2 even-odd line products of one pass, thread t taking tasks t,
-// t + T, ...: lines along r read i0 and write o0, along s i1 / o1, along t
-// i2 / o2 (task order and line geometry as line_of).  A warp whose 32 tasks
-// lie in one direction takes that direction's constant-stride body; a warp
-// that straddles two directions (N^2 is rarely a multiple of 32) takes the
-// runtime-stride body for all its lanes, so no warp runs two bodies one
-// after the other.
-template <int N, int T>
-__device__ __forceinline__ void line_eo_pass(const float2 *i0, const float2 *i1, const float2 *i2, float2 *o0,
-                                             float2 *o1, float2 *o2, const EoMat<N> &M) {
-    constexpr int N2 = N * N;
-    static_assert(T % 32 == 0, "warp-aligned task groups");
-    for (int task = threadIdx.x; task < 3 * N2; task += T) {
-        const int first = task & ~31;
-        const int last = first + 31 < 3 * N2 - 1 ? first + 31 : 3 * N2 - 1;
-        const int d = first / N2;
-        if (d != last / N2) {                    // warp-uniform
-            int stride;
-            const int base = line_of<N>(task, stride);
-            const float2 *in = task < N2 ? i0 : (task < 2 * N2 ? i1 : i2);
-            float2 *out = task < N2 ? o0 : (task < 2 * N2 ? o1 : o2);
-            line_eo<N>(in, out, base, stride, M);
-        } else if (d == 0) {
-            line_eo_s<N, 1>(i0 + N * task, o0 + N * task, M);
-        } else if (d == 1) {
-            const int c = task - N2;
-            const int base = c % N + N2 * (c / N);
-            line_eo_s<N, N>(i1 + base, o1 + base, M);
-        } else {
-            const int c = task - 2 * N2;
-            line_eo_s<N, N2>(i2 + c, o2 + c, M);
-        }
-    }
-}
-
 template <int N, bool EO>
 struct DfConsts;
 template <int N>

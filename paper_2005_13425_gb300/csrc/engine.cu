@@ -120,7 +120,12 @@ __device__ __forceinline__ double eng_head_tile(const ProbDesc &P, int64_t e0, i
         const bool odd = (e - e0) & 1;
         float2 *X = odd ? S1 : S0;
         float2 *F0 = odd ? S0 : S1;
-        line_eo_pass<N, T>(X, X, X, F0, S2, S3, D.fwd);
+        for (int task = t; task < 3 * N2; task += T) {
+            int stride;
+            const int base = line_of<N>(task, stride);
+            float2 *Fd = task < N2 ? F0 : (task < 2 * N2 ? S2 : S3);
+            line_eo<N>(X, Fd, base, stride, D.fwd);
+        }
         __syncthreads();
         const float2 *g = P.g + e * 6 * N3;
         for (int q = t; q < N3; q += T) {
@@ -141,7 +146,13 @@ __device__ __forceinline__ double eng_head_tile(const ProbDesc &P, int64_t e0, i
             S3[q] = dfa::norm(ut);
         }
         __syncthreads();
-        line_eo_pass<N, T>(F0, S2, S3, X, S4, S5, D.bwd);
+        for (int task = t; task < 3 * N2; task += T) {
+            int stride;
+            const int base = line_of<N>(task, stride);
+            const float2 *Fd = task < N2 ? F0 : (task < 2 * N2 ? S2 : S3);
+            float2 *Pd = task < N2 ? X : (task < 2 * N2 ? S4 : S5);
+            line_eo<N>(Fd, Pd, base, stride, D.bwd);
+        }
         __syncthreads();
         {
             int ex, ey, ez;
