@@ -208,9 +208,9 @@ __device__ __forceinline__ u128 cg_head_pipelined(const AxDfArgs &a, double beta
             dfa::Acc ut = dfa::first(g2.x, g2.y, wr.x, wr.y);
             dfa::fma(ut, g4.x, g4.y, ws.x, ws.y);
             dfa::fma(ut, g5.x, g5.y, wt.x, wt.y);
-            F0[q] = dfa::norm(ur);
-            S2[q] = dfa::norm(us);
-            S3[q] = dfa::norm(ut);
+            F0[q] = dfa::raw(ur);
+            S2[q] = dfa::raw(us);
+            S3[q] = dfa::raw(ut);
         }
         __syncthreads();
         // backward: the three partials of w, into X (consumed), S4, S5

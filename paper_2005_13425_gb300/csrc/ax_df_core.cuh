@@ -25,6 +25,7 @@ struct DfMat {
 //   Q_m = sum_{l<H} b(m,l) xs_l + b(m,H) x_H, b(m,l) = (M(m,l) - M(N-1-m,l))/2
 // and for odd N the middle output y_H = sum_{l<H} M(H,l) xd_l + M(H,H) x_H.
 // This halves the products of a line (Solomonoff's even-odd decomposition).
+// The outputs are stored as unnormalised pairs (dfa::add_acc_raw).
 template <int N>
 struct EoMat {
     static constexpr int H = N / 2;
@@ -138,8 +139,8 @@ __device__ __forceinline__ void line_eo(const float2 *in, float2 *out, int base,
 #pragma unroll
         for (int l = 1; l < H; l++) dfa::fma(Q, M.bh[m * (H + 1) + l], M.bl[m * (H + 1) + l], sh[l], sl[l]);
         if (N & 1) dfa::fma(Q, M.bh[m * (H + 1) + H], M.bl[m * (H + 1) + H], ch, cl);
-        out[base + m * stride] = dfa::add_acc(P, Q, 1.f);
-        out[base + (N - 1 - m) * stride] = dfa::add_acc(P, Q, -1.f);
+        out[base + m * stride] = dfa::add_acc_raw(P, Q, 1.f);
+        out[base + (N - 1 - m) * stride] = dfa::add_acc_raw(P, Q, -1.f);
     }
     if (N & 1) {
         dfa::Acc Y = dfa::first(M.ch[0], M.cl[0], dh[0], dl[0]);
@@ -284,9 +285,9 @@ __device__ __forceinline__ void df_element(const DfElemIO &io, double beta, doub
         dfa::Acc tt = dfa::first(g2.x, g2.y, wr.x, wr.y);
         dfa::fma(tt, g4.x, g4.y, ws.x, ws.y);
         dfa::fma(tt, g5.x, g5.y, wt.x, wt.y);
-        W0[q] = dfa::norm(r);
-        W1[q] = dfa::norm(s);
-        W2[q] = dfa::norm(tt);
+        W0[q] = dfa::raw(r);
+        W1[q] = dfa::raw(s);
+        W2[q] = dfa::raw(tt);
     }
     __syncthreads();
 

@@ -79,6 +79,22 @@ __device__ __forceinline__ float2 add_acc(const Acc &P, const Acc &Q, float sgn)
     return make_float2(h, l);
 }
 
+// (P.s + P.c) + sgn*(Q.s + Q.c) as an unnormalised pair (s, e): the
+// leading parts added by TwoSum, the compensations folded into e, without
+// the final Fast2Sum.  |e| stays within a few ulps of s, which is all the
+// consumers need (the cross terms of the next products, pair additions and
+// the FP64 reassembly s + e are exact or accurate for such pairs); it saves
+// three operations per value.
+__device__ __forceinline__ float2 add_acc_raw(const Acc &P, const Acc &Q, float sgn) {
+    float s, e;
+    two_sum(P.s, sgn * Q.s, s, e);
+    return make_float2(s, __fadd_rn(e, __fadd_rn(P.c, sgn * Q.c)));
+}
+
+// The accumulator (s, c) itself as an unnormalised pair (|c| is a few ulps
+// of s at most), for the same consumers as add_acc_raw.
+__device__ __forceinline__ float2 raw(const Acc &a) { return make_float2(a.s, a.c); }
+
 // Compensated FP32 accumulation of products of floats (Dot2 on single
 // values): s + c carries sum(a*b) to about 2^-47 relative, with FP32
 // instructions only.  value() returns the FP64 total.

@@ -141,9 +141,9 @@ __device__ __forceinline__ double eng_head_tile(const ProbDesc &P, int64_t e0, i
             dfa::Acc ut = dfa::first(g2.x, g2.y, wr.x, wr.y);
             dfa::fma(ut, g4.x, g4.y, ws.x, ws.y);
             dfa::fma(ut, g5.x, g5.y, wt.x, wt.y);
-            F0[q] = dfa::norm(ur);
-            S2[q] = dfa::norm(us);
-            S3[q] = dfa::norm(ut);
+            F0[q] = dfa::raw(ur);
+            S2[q] = dfa::raw(us);
+            S3[q] = dfa::raw(ut);
         }
         __syncthreads();
         for (int task = t; task < 3 * N2; task += T) {

@@ -29,20 +29,22 @@ FP32_PEAK_TOPS = GB300_SMS * FP32_LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
 
 # FP32-pipe instructions of the double-float building blocks (df.cuh):
 # TwoSum 6; first product (TwoProd + cross terms) 4; Dot2 step 12;
-# normalisation 3; pair addition 11.
-_TWO_SUM, _FIRST, _DOT2, _NORM, _ADD = 6, 4, 12, 3, 11
+# normalisation 3; pair addition 11; the unnormalised pair addition of the
+# line outputs (add_acc_raw) 8.
+_TWO_SUM, _FIRST, _DOT2, _NORM, _ADD, _ADD_RAW = 6, 4, 12, 3, 11, 8
 
 
 def df_line_ops(n: int) -> int:
     """FP32 instructions of one even-odd line product of n points: n/2 pair
     sums and differences, then per output pair two Dot2 sums of n/2 terms
-    and two pair additions; odd n adds the middle term and middle output."""
+    and two unnormalised pair additions; odd n adds the middle term and the
+    (normalised) middle output."""
     h = n // 2
     ops = 2 * h * _ADD
     if n % 2 == 0:
-        ops += h * (2 * (_FIRST + _DOT2 * (h - 1)) + 2 * _ADD)
+        ops += h * (2 * (_FIRST + _DOT2 * (h - 1)) + 2 * _ADD_RAW)
     else:
-        ops += h * (2 * (_FIRST + _DOT2 * (h - 1)) + _DOT2 + 2 * _ADD)
+        ops += h * (2 * (_FIRST + _DOT2 * (h - 1)) + _DOT2 + 2 * _ADD_RAW)
         ops += _FIRST + _DOT2 * h + _NORM
     return ops
 
@@ -51,11 +53,11 @@ def df_fp32_ops_per_point(n: int) -> float:
     """FP32 instructions per point of the double-float ax_e (algorithmic:
     the operation counts of the arithmetic as written, no overheads):
     3 forward and 3 backward line products per point, the geometric
-    contraction (3 Dot2 sums of 3 terms, normalised), the sum of the three
-    partials (2 pair additions) and the 2 FP32 operations of the input
+    contraction (3 Dot2 sums of 3 terms, kept unnormalised), the sum of the
+    three partials (2 pair additions) and the 2 FP32 operations of the input
     split."""
     lines = 6 * df_line_ops(n) / n
-    contraction = 3 * (_FIRST + 2 * _DOT2 + _NORM)
+    contraction = 3 * (_FIRST + 2 * _DOT2)
     return lines + contraction + 2 * _ADD + 2
 
 
