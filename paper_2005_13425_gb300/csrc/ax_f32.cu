@@ -128,18 +128,6 @@ ax_f32_staged_kernel(AxF32Args a, CgScalars *err, const __grid_constant__ F32Mat
     if (t == 0 && e < a.E) issue(e, 0);
     issued[0] = e < a.E ? 1 : 0;
     bool ok = true;
-    // The final pass of each element runs at the start of the next one's
-    // update phase (it reads only the backward partials and registers), so
-    // an element costs five barriers: the stage wait, then after the
-    // update, the forward, the contraction and the backward passes.
-    float pv[f32_points_per_thread<N, T>()];
-    int64_t e_prev = -1;
-    auto finish = [&](int64_t ep) {
-        int ex = 0, ey = 0, ez = 0;
-        if (MODE == 1) element_coords(ep, a.m, ex, ey, ez);
-        f32_final_staged<N, MODE, T>(smf + 2 * STAGE, a.w + ep * N3, MODE == 1 ? box_faces(ex, ey, ez, a.m) : 0u,
-                                     pv, dot, pf);
-    };
     for (int i = 0; e < a.E; e += gridDim.x, i++) {
         const int s = i & 1;
         const int64_t en = e + gridDim.x;
@@ -152,16 +140,15 @@ ax_f32_staged_kernel(AxF32Args a, CgScalars *err, const __grid_constant__ F32Mat
                                        : mbar_wait(&bars[s], waited[s] & 1)) != 0;
         if (!ok) break;
         waited[s]++;
-        if (e_prev >= 0) finish(e_prev);
         F32StagedOut o;
         o.p = MODE == 1 ? a.p + e * N3 : nullptr;
         o.x = MODE == 1 ? a.x + e * N3 : nullptr;
         o.w = a.w + e * N3;
-        f32_front_staged<N, MODE, T>(smf + s * STAGE, smf + 2 * STAGE, a.g + e * 6 * N3, o, beta, xa, D, pv);
-        __syncthreads();
-        e_prev = e;
+        int ex = 0, ey = 0, ez = 0;
+        if (MODE == 1) element_coords(e, a.m, ex, ey, ez);
+        f32_element_staged<N, MODE, T>(smf + s * STAGE, smf + 2 * STAGE, a.g + e * 6 * N3, o, beta, xa, ex, ey,
+                                       ez, a.m, D, dot, pf);
     }
-    if (ok && e_prev >= 0) finish(e_prev);
     if (!ok) {   // drain the copies in flight before leaving, then report
         if (t == 0) {
             for (int s = 0; s < 2; s++)

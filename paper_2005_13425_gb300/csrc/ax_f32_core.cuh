@@ -288,17 +288,15 @@ struct F32StagedOut {
     float *w;   // ax_e output
 };
 
-// Front of a staged element (whole CTA; contains barriers): the geometric
-// factors of the thread's points into registers, the update (MODE 1: p =
-// r + beta p, x += xa p_old, written back; pv keeps the thread's new p),
-// the forward derivatives, their geometric contraction and the backward
-// partials into W + 3n^3 .. W + 6n^3.  It ends after the backward pass,
-// before the barrier the caller places; the stage is not read after the
-// forward pass (its fence for the copy engine is issued there).
+// Element body on stage `st` (whole CTA); g: the element's geometric
+// factors [6][n^3] in global memory.  pf: the thread's point-face masks
+// (f32_point_masks).  Ends with fence + barrier, after which the stage may
+// be refilled.
 template <int N, int MODE, int T>
-__device__ __forceinline__ void f32_front_staged(float *st, float *W, const float *__restrict__ g,
-                                                 const F32StagedOut &o, float beta, float xa, const F32Mat<N> &D,
-                                                 float *pv) {
+__device__ __forceinline__ void f32_element_staged(float *st, float *W, const float *__restrict__ g,
+                                                   const F32StagedOut &o, float beta, float xa, int ex, int ey,
+                                                   int ez, const Mesh &m, const F32Mat<N> &D, dfa::Acc32 &dot,
+                                                   const unsigned *pf) {
     constexpr int N3 = N * N * N;
     constexpr int PPT = f32_points_per_thread<N, T>();
     constexpr bool RAGGED = PPT * T != N3;
@@ -320,22 +318,25 @@ __device__ __forceinline__ void f32_front_staged(float *st, float *W, const floa
     }
     if (MODE == 1) {
         float *R = st, *P = st + N3, *Z = st + 2 * N3;
-#pragma unroll
-        for (int k = 0; k < PPT; k++) {
-            const int q = t + k * T;
-            if (RAGGED && q >= N3) break;
-            const float pold = P[q];
-            const float pn = fmaf(beta, pold, R[q]);
-            P[q] = pn;
-            o.p[q] = pn;
-            if (xa != 0.f) o.x[q] = fmaf(xa, pold, Z[q]);
-            pv[k] = pn;
+        if (xa != 0.f) {
+            for (int q = t; q < N3; q += T) {
+                const float pold = P[q];
+                const float pn = fmaf(beta, pold, R[q]);
+                P[q] = pn;
+                o.p[q] = pn;
+                o.x[q] = fmaf(xa, pold, Z[q]);
+            }
+        } else {
+            for (int q = t; q < N3; q += T) {
+                const float pn = fmaf(beta, P[q], R[q]);
+                P[q] = pn;
+                o.p[q] = pn;
+            }
         }
         U = P;
         __syncthreads();
     }
     f32_line_pass<N, T, false>(U, U, U, W0, W1, W2, D);
-    fence_proxy_async();                       // the last read of the stage by this thread
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
@@ -348,20 +349,8 @@ __device__ __forceinline__ void f32_front_staged(float *st, float *W, const floa
     }
     __syncthreads();
     f32_line_pass<N, T, true>(W0, W1, W2, P0, P1, P2, D);
-}
-
-// Final pass of a staged element (no barrier; reads only the backward
-// partials and the thread's registers): w = the sum of the partials, and
-// in MODE 1 box-face points zeroed and the local products w p (p from pv)
-// added to dot.  bf: the element's box faces (MODE 1).
-template <int N, int MODE, int T>
-__device__ __forceinline__ void f32_final_staged(const float *W, float *w, unsigned bf, const float *pv,
-                                                 dfa::Acc32 &dot, const unsigned *pf) {
-    constexpr int N3 = N * N * N;
-    constexpr int PPT = f32_points_per_thread<N, T>();
-    constexpr bool RAGGED = PPT * T != N3;
-    const float *P0 = W + 3 * N3, *P1 = W + 4 * N3, *P2 = W + 5 * N3;
-    const int t = threadIdx.x;
+    __syncthreads();
+    const unsigned bf = MODE == 1 ? box_faces(ex, ey, ez, m) : 0u;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
         const int q = t + k * T;
@@ -371,24 +360,11 @@ __device__ __forceinline__ void f32_final_staged(const float *W, float *w, unsig
             if (pf[k] & bf)
                 wv = 0.f;
             else
-                dot.add_prod(wv, pv[k]);
+                dot.add_prod(wv, U[q]);
         }
-        w[q] = wv;
+        o.w[q] = wv;
     }
-}
-
-// A whole staged element (front, barrier, final, barrier), after which the
-// stage may be refilled.  pf: the thread's point-face masks
-// (f32_point_masks).
-template <int N, int MODE, int T>
-__device__ __forceinline__ void f32_element_staged(float *st, float *W, const float *__restrict__ g,
-                                                   const F32StagedOut &o, float beta, float xa, int ex, int ey,
-                                                   int ez, const Mesh &m, const F32Mat<N> &D, dfa::Acc32 &dot,
-                                                   const unsigned *pf) {
-    float pv[f32_points_per_thread<N, T>()];
-    f32_front_staged<N, MODE, T>(st, W, g, o, beta, xa, D, pv);
-    __syncthreads();
-    f32_final_staged<N, MODE, T>(W, o.w, MODE == 1 ? box_faces(ex, ey, ez, m) : 0u, pv, dot, pf);
+    fence_proxy_async();
     __syncthreads();
 }
 
