@@ -209,3 +209,27 @@ def test_partitioned_box_two_gloo_ranks(oracle, tmp_path):
     w = np.concatenate([p["w"] for p in parts])
     x = np.concatenate([p["x"] for p in parts])
     check_against_oracle(oracle, w, x, meta[0]["it"], meta[0]["hist"], meta[0]["bad"])
+
+
+@pytest.mark.parametrize("dims,n,parts", [((2, 3, 4), 2, 4), ((3, 1, 5), 3, 2), ((1, 1, 3), 4, 3),
+                                          ((2, 2, 7), 6, 5), ((4, 3, 2), 5, 2), ((1, 2, 9), 3, 9)])
+def test_partitioned_operator_bit_exact_over_layouts(oracle, dims, n, parts):
+    """The interface protocol over uneven slab counts, slabs one element
+    layer thick, meshes one element wide and n = 2..6: the assembled
+    operator equals the single-box mask(dssum(ax_e)) bit for bit."""
+    P = oracle.box_problem(*dims, n, inputs.PERTURB_AMP, inputs.perturbation_coeffs(parts))
+    u = inputs.local_field(P["E"], n, seed=parts + n)
+    bounds = partition.slab_bounds(dims[2], parts)
+    slabs = [OracleSlab(oracle, P, dims, n, z0, z1) for z0, z1 in bounds]
+    per = dims[0] * dims[1]
+    box = partition.PartitionedBox(slabs, partition.Exchange(parts, 0, parts))
+    us = [torch.from_numpy(np.ascontiguousarray(u[z0 * per:z1 * per])) for z0, z1 in bounds]
+    ws = [s.new_field() for s in slabs]
+    box.apply(us, ws)
+    got = np.concatenate([w.numpy() for w in ws])
+    assert np.array_equal(got, oracle.apply_A(*dims, n, P["D"], P["gxyz"], P["mask"], u))
+    # the slab shares of <a,b>_c add up to the whole box's
+    a = [torch.from_numpy(np.ascontiguousarray(got[z0 * per:z1 * per])) for z0, z1 in bounds]
+    tot = box.dots([(a, us)])[0]
+    want = oracle.dot_c(*dims, n, got, u)
+    assert abs(tot - want) <= 1e-13 * max(abs(want), 1e-300) * P["E"]
