@@ -3,7 +3,8 @@ one process, the interface exchanges as device copies between them.
 
 * The assembled operator over the slabs equals the single-box nb_apply bit
   for bit (same device-built geometry per element, the interface sums
-  continued in ascending element order).
+  continued in ascending element order), including slabs one element layer
+  thick, meshes one element wide, n = 2..12 and 16^3 elements in two slabs.
 * CG over the slabs follows the single-box solver and the oracle's CG
   (rho history and x to 1e-8 after fixed iterations).
 * Whole-box calls on a slab context are refused.
@@ -47,7 +48,9 @@ def split(a, dims, parts):
             for z0, z1 in partition.slab_bounds(dims[2], parts)]
 
 
-@pytest.mark.parametrize("dims,n,parts", [((5, 4, 7), 8, 3), ((3, 2, 4), 5, 4), ((16, 16, 16), 10, 2)])
+@pytest.mark.parametrize("dims,n,parts", [((5, 4, 7), 8, 3), ((3, 2, 4), 5, 4), ((16, 16, 16), 10, 2),
+                                          ((1, 1, 3), 4, 3), ((2, 1, 5), 3, 5), ((1, 3, 2), 2, 2),
+                                          ((4, 4, 6), 12, 4)])
 def test_slab_operator_equals_single_box(nek, oracle, dims, n, parts):
     s = inputs.perturbation_coeffs(inputs.SEED_MESH)
     E = dims[0] * dims[1] * dims[2]
