@@ -88,6 +88,19 @@ typedef struct {
 /* Set-up and tear-down                                                  */
 /* --------------------------------------------------------------------- */
 
+/* Environment switches (all optional; the first two and the test switches
+ * below are read when a context or an engine is set up):
+ *   NEKGB_F32_STAGED=0        FP32 heads without bulk-copy staging.
+ *   NEKGB_TUNE_CACHE=<file>   the engine's autotuner cache (see the engine).
+ *   NEKGB_FAIL_ALLOC=<k>      tests: the k-th device allocation of the
+ *       process fails (host-side fault injection).
+ *   NEKGB_TEST_UNARMED_WAIT_NS=<ns>  tests: each CTA's first wait in the
+ *       staged FP32 head uses a barrier that nothing arrives on, with this
+ *       limit, so the solve ends with NB_ERR_TIMEOUT (bounded-wait path).
+ *   NEKGB_TEST_DOT_SHIFT=<k>  tests: shifts the scale of the FP64 head's
+ *       exact <w,p>_c sum by 2^k, to exercise its range check
+ *       (NB_ERR_BREAKDOWN). */
+
 /* Build a context for the box `mesh` with n GLL points per direction from
  * caller-supplied operator data (the inputs of Listing 1).
  *   D     host, n*n doubles, D[i*n+l] = dxm1(i,l).

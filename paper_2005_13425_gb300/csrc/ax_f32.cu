@@ -128,6 +128,8 @@ ax_f32_staged_kernel(AxF32Args a, CgScalars *err, const __grid_constant__ F32Mat
     if (t == 0 && e < a.E) issue(e, 0);
     issued[0] = e < a.E ? 1 : 0;
     bool ok = true;
+    float gv[f32_points_per_thread<N, T>()][6];
+    if (e < a.E) f32_load_factors<N, T>(a.g + e * 6 * N3, gv);
     for (int i = 0; e < a.E; e += gridDim.x, i++) {
         const int s = i & 1;
         const int64_t en = e + gridDim.x;
@@ -146,8 +148,8 @@ ax_f32_staged_kernel(AxF32Args a, CgScalars *err, const __grid_constant__ F32Mat
         o.w = a.w + e * N3;
         int ex = 0, ey = 0, ez = 0;
         if (MODE == 1) element_coords(e, a.m, ex, ey, ez);
-        f32_element_staged<N, MODE, T>(smf + s * STAGE, smf + 2 * STAGE, a.g + e * 6 * N3, o, beta, xa, ex, ey,
-                                       ez, a.m, D, dot, pf);
+        f32_element_staged<N, MODE, T>(smf + s * STAGE, smf + 2 * STAGE, gv, en < a.E ? a.g + en * 6 * N3 : nullptr,
+                                       o, beta, xa, ex, ey, ez, a.m, D, dot, pf);
     }
     if (!ok) {   // drain the copies in flight before leaving, then report
         if (t == 0) {

@@ -273,7 +273,26 @@ __host__ __device__ constexpr int f32_staged_smem_floats() {
 template <int N>
 __host__ __device__ constexpr int f32_staged_min_blocks() {
     constexpr int by_smem = (228 * 1024) / (4 * f32_staged_smem_floats<N, 1>() + 1024);
-    return by_smem < 4 ? (by_smem < 1 ? 1 : by_smem) : 4;
+    return by_smem < 3 ? (by_smem < 1 ? 1 : by_smem) : 3;
+}
+
+// Geometric factors of a thread's points, gv[k][c] = g[c n^3 + t + k T]
+// (streaming loads; zero past the element's last point).
+template <int N, int T>
+__device__ __forceinline__ void f32_load_factors(const float *__restrict__ g, float (&gv)[f32_points_per_thread<N, T>()][6]) {
+    constexpr int N3 = N * N * N;
+    constexpr int PPT = f32_points_per_thread<N, T>();
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        const int q = threadIdx.x + k * T;
+        if (PPT * T == N3 || q < N3) {
+#pragma unroll
+            for (int c = 0; c < 6; c++) gv[k][c] = __ldcs(g + c * N3 + q);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 6; c++) gv[k][c] = 0.f;
+        }
+    }
 }
 
 template <int N>
@@ -288,15 +307,18 @@ struct F32StagedOut {
     float *w;   // ax_e output
 };
 
-// Element body on stage `st` (whole CTA); g: the element's geometric
-// factors [6][n^3] in global memory.  pf: the thread's point-face masks
-// (f32_point_masks).  Ends with fence + barrier, after which the stage may
-// be refilled.
+// Element body on stage `st` (whole CTA).  gv holds this element's
+// geometric factors on entry (f32_load_factors); right after the
+// contraction consumes them it is refilled from gnext, the next element's
+// factors (null: none), so those loads are in flight through the rest of
+// this element and the next one's update and forward passes.  pf: the
+// thread's point-face masks (f32_point_masks).  Ends with fence + barrier,
+// after which the stage may be refilled.
 template <int N, int MODE, int T>
-__device__ __forceinline__ void f32_element_staged(float *st, float *W, const float *__restrict__ g,
-                                                   const F32StagedOut &o, float beta, float xa, int ex, int ey,
-                                                   int ez, const Mesh &m, const F32Mat<N> &D, dfa::Acc32 &dot,
-                                                   const unsigned *pf) {
+__device__ __forceinline__ void f32_element_staged(float *st, float *W, float (&gv)[f32_points_per_thread<N, T>()][6],
+                                                   const float *__restrict__ gnext, const F32StagedOut &o,
+                                                   float beta, float xa, int ex, int ey, int ez, const Mesh &m,
+                                                   const F32Mat<N> &D, dfa::Acc32 &dot, const unsigned *pf) {
     constexpr int N3 = N * N * N;
     constexpr int PPT = f32_points_per_thread<N, T>();
     constexpr bool RAGGED = PPT * T != N3;
@@ -304,18 +326,6 @@ __device__ __forceinline__ void f32_element_staged(float *st, float *W, const fl
     float *W0 = W, *W1 = W + N3, *W2 = W + 2 * N3;
     float *P0 = W + 3 * N3, *P1 = W + 4 * N3, *P2 = W + 5 * N3;
     const int t = threadIdx.x;
-    float gv[PPT][6];
-#pragma unroll
-    for (int k = 0; k < PPT; k++) {
-        const int q = t + k * T;
-        if (!RAGGED || q < N3) {
-#pragma unroll
-            for (int c = 0; c < 6; c++) gv[k][c] = __ldcs(g + c * N3 + q);
-        } else {
-#pragma unroll
-            for (int c = 0; c < 6; c++) gv[k][c] = 0.f;
-        }
-    }
     if (MODE == 1) {
         float *R = st, *P = st + N3, *Z = st + 2 * N3;
         if (xa != 0.f) {
@@ -347,6 +357,7 @@ __device__ __forceinline__ void f32_element_staged(float *st, float *W, const fl
         W1[q] = fmaf(gv[k][1], wr, fmaf(gv[k][3], ws, gv[k][4] * wt));
         W2[q] = fmaf(gv[k][2], wr, fmaf(gv[k][4], ws, gv[k][5] * wt));
     }
+    if (gnext) f32_load_factors<N, T>(gnext, gv);
     __syncthreads();
     f32_line_pass<N, T, true>(W0, W1, W2, P0, P1, P2, D);
     __syncthreads();

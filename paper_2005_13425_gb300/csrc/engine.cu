@@ -584,6 +584,8 @@ eng_m_head_staged(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, c
     if (t == 0) issue(cur, 0);
     unsigned pf[f32_points_per_thread<N, T>()];
     f32_point_masks<N, T>(pf);
+    float gv[f32_points_per_thread<N, T>()][6];
+    f32_load_factors<N, T>(desc[tiles[cur.ti].x].g32 + cur.e * 6 * N3, gv);
     dfa::Acc32 dot;
     bool ok = true;
     for (int i = 0;; i++) {
@@ -607,8 +609,9 @@ eng_m_head_staged(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, c
         o.w = P.w32 + cur.e * N3;
         int ex, ey, ez;
         element_coords(cur.e, P.m, ex, ey, ez);
-        f32_element_staged<N, 1, T>(smf + s * STAGE, smf + 2 * STAGE, P.g32 + cur.e * 6 * N3, o, beta, xa, ex, ey,
-                                    ez, P.m, D, dot, pf);
+        f32_element_staged<N, 1, T>(smf + s * STAGE, smf + 2 * STAGE, gv,
+                                    more ? desc[tiles[nxt.ti].x].g32 + nxt.e * 6 * N3 : nullptr, o, beta, xa, ex,
+                                    ey, ez, P.m, D, dot, pf);
         if (cur.e + 1 == cur.e1) {   // the tile is complete
             const double b = block_sum(dot.value(), red);
             dot = dfa::Acc32();
