@@ -30,6 +30,51 @@ namespace nekgb {
 
 constexpr int kAsmThreads = 256;
 
+// The shared nodes q in [a, b) with C copies each that fall to this thread
+// (q = tid mod S, the same round-robin over all shared nodes as one loop
+// would give), U of them per step: every load of a step is issued before
+// the first sum, so each thread keeps up to U (C + 1) loads in flight.  The
+// copies are summed in ascending element order (the dssum order), r is
+// updated once and written to every copy.
+template <int N, int C, int U, typename T, typename Sq>
+__device__ __forceinline__ void update_nodes(T *__restrict__ r, const T *__restrict__ w, const DsCat &dd,
+                                             int a, int b, int tid, int S, T alpha, Sq &add_sq) {
+    const int first = a + ((tid - a % S) % S + S) % S;
+    for (int64_t q = first; q < b; q += (int64_t)U * S) {
+        int64_t i0[U];
+        int kind[U];
+        T v[U][C], rv[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int64_t qu = q + u * S;
+            kind[u] = 0;
+            i0[u] = 0;
+            if (qu < b) {
+                if constexpr (C == 2) i0[u] = face_first<N>((int)qu, dd, kind[u]);
+                else if constexpr (C == 4) i0[u] = edge_first<N>((int)qu, dd, kind[u]);
+                else i0[u] = vertex_first<N>((int)qu, dd);
+                v[u][0] = __ldcs(w + i0[u]);
+#pragma unroll
+                for (int k = 1; k < C; k++) v[u][k] = __ldcs(w + i0[u] + copy_offset<N, C>(k, kind[u], dd));
+                rv[u] = r[i0[u]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            if (q + u * S < b) {
+                T s = plus_zero(v[u][0]);
+#pragma unroll
+                for (int k = 1; k < C; k++) s = s + v[u][k];
+                const T rn = fma(-alpha, s, rv[u]);
+                r[i0[u]] = rn;
+#pragma unroll
+                for (int k = 1; k < C; k++) r[i0[u] + copy_offset<N, C>(k, kind[u], dd)] = rn;
+                add_sq(rn);
+            }
+        }
+    }
+}
+
 template <typename T, int N>
 __global__ void __launch_bounds__(kAsmThreads, 5)
 assemble_update_kernel(T *__restrict__ r, const T *__restrict__ w, Mesh m, DsCat dd, CgScalars *sc,
@@ -50,56 +95,56 @@ assemble_update_kernel(T *__restrict__ r, const T *__restrict__ w, Mesh m, DsCat
             sq.add_sq(v.x, v.y, 1.f);
         }
     };
-    // element-interior points, element by element
+    // element-interior points: each step takes UE elements (KI points of
+    // each for this thread) and issues the loads of CH points before their
+    // updates, so up to 2 CH loads are in flight per thread
     if constexpr (N > 2) {
         constexpr int NI = N - 2, NI3 = NI * NI * NI;
         constexpr int KI = (NI3 + kAsmThreads - 1) / kAsmThreads;
+        constexpr int UE = KI >= 4 ? 1 : 4 / KI, NB = UE * KI, CH = F32 ? 6 : 4;
         int qk[KI];
+        bool ok[KI];
 #pragma unroll
         for (int k = 0; k < KI; k++) {
             const int qi = threadIdx.x + k * kAsmThreads;
             const int a = qi % NI, b = (qi / NI) % NI, c = qi / (NI * NI);
             qk[k] = (1 + a) + N * (1 + b) + N * N * (1 + c);
+            ok[k] = KI * kAsmThreads == NI3 || qi < NI3;
         }
-        for (int64_t e = blockIdx.x; e < m.E; e += gridDim.x) {
-            const int64_t base = e * N3;
+        for (int64_t e = blockIdx.x; e < m.E; e += (int64_t)UE * gridDim.x) {
 #pragma unroll
-            for (int k = 0; k < KI; k++) {
-                if (KI * kAsmThreads != NI3 && threadIdx.x + k * kAsmThreads >= NI3) break;
-                const int64_t q = base + qk[k];
-                const T rn = fma(-alpha, __ldcs(w + q), r[q]);
-                r[q] = rn;
-                add_sq(rn);
+            for (int j0 = 0; j0 < NB; j0 += CH) {
+                T wv[CH], rv[CH];
+                int64_t qa[CH];
+                bool go[CH];
+#pragma unroll
+                for (int jj = 0; jj < CH; jj++) {
+                    const int j = j0 + jj, u = j / KI, k = j % KI;
+                    const int64_t eu = e + (int64_t)u * gridDim.x;
+                    go[jj] = j < NB && ok[k] && eu < m.E;
+                    qa[jj] = eu * N3 + qk[k];
+                    if (go[jj]) {
+                        wv[jj] = __ldcs(w + qa[jj]);
+                        rv[jj] = r[qa[jj]];
+                    }
+                }
+#pragma unroll
+                for (int jj = 0; jj < CH; jj++) {
+                    if (go[jj]) {
+                        const T rn = fma(-alpha, wv[jj], rv[jj]);
+                        r[qa[jj]] = rn;
+                        add_sq(rn);
+                    }
+                }
             }
         }
     }
-    // shared nodes
-    const int total = dd.o[7];
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
-        int64_t idx[8];
-        const int c = cat_copies<N>(q, dd, idx);
-        T s;
-        if (c == 2) {
-            s = plus_zero(__ldcs(w + idx[0])) + __ldcs(w + idx[1]);
-        } else if (c == 4) {
-            T a[4];
-#pragma unroll
-            for (int k = 0; k < 4; k++) a[k] = __ldcs(w + idx[k]);
-            s = plus_zero(a[0]);
-#pragma unroll
-            for (int k = 1; k < 4; k++) s = s + a[k];
-        } else {
-            T a[8];
-#pragma unroll
-            for (int k = 0; k < 8; k++) a[k] = __ldcs(w + idx[k]);
-            s = plus_zero(a[0]);
-#pragma unroll
-            for (int k = 1; k < 8; k++) s = s + a[k];
-        }
-        const T rn = fma(-alpha, s, r[idx[0]]);
-        for (int k = 0; k < c; k++) r[idx[k]] = rn;
-        add_sq(rn);
-    }
+    // shared nodes, one copy count at a time
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int S = gridDim.x * blockDim.x;
+    update_nodes<N, 2, F32 ? 3 : 2>(r, w, dd, dd.o[0], dd.o[3], tid, S, alpha, add_sq);
+    update_nodes<N, 4, F32 ? 2 : 1>(r, w, dd, dd.o[3], dd.o[6], tid, S, alpha, add_sq);
+    update_nodes<N, 8, 1>(r, w, dd, dd.o[6], dd.o[7], tid, S, alpha, add_sq);
     double v[1], tot[1];
     if constexpr (F32) v[0] = acc32.value();
     else v[0] = sq.value() * __longlong_as_double((long long)(1023 - 2 * sh) << 52);

@@ -175,4 +175,102 @@ __device__ __forceinline__ int cat_copies(int q, const DsCat &d, int64_t *idx) {
     return 8;
 }
 
+
+// ------------------------------------------------ first copy + fixed offsets
+// The same enumeration as cat_copies, one category at a time, returning only
+// the first copy of node q and which of the category's three kinds it is
+// (x, y or z face; the edge along z, y or x; vertices have one kind): the
+// other copies sit at offsets that depend on the kind and the mesh only
+// (copy_offset), so a caller keeps one index per node instead of eight.
+template <int N>
+__device__ __forceinline__ int64_t face_first(int q, const DsCat &d, int &kind) {
+    constexpr int N1 = N - 1, N2 = N * N;
+    constexpr int64_t N3 = (int64_t)N * N * N;
+    const int64_t sy = d.ex, sz = (int64_t)d.ex * d.ey;
+    unsigned t, r0, r1;
+    int ex, ey, ez, lx, ly, lz;
+    if (q < d.o[1]) {
+        kind = 0;
+        divmod((unsigned)q, d.fNYp, t, r0);
+        divmod(t, d.fNZp, t, r1);
+        nonplane_elem<N>((int)r0, d.ey, ey, ly);
+        nonplane_elem<N>((int)r1, d.ez, ez, lz);
+        return ((int64_t)t + sy * ey + sz * ez) * N3 + N1 + N * ly + N2 * lz;
+    }
+    if (q < d.o[2]) {
+        kind = 1;
+        divmod((unsigned)(q - d.o[1]), d.fNXp, t, r0);
+        divmod(t, d.fNZp, t, r1);
+        nonplane_elem<N>((int)r0, d.ex, ex, lx);
+        nonplane_elem<N>((int)r1, d.ez, ez, lz);
+        return (ex + sy * (int64_t)t + sz * ez) * N3 + lx + N * N1 + N2 * lz;
+    }
+    kind = 2;
+    divmod((unsigned)(q - d.o[2]), d.fNXp, t, r0);
+    divmod(t, d.fNYp, t, r1);
+    nonplane_elem<N>((int)r0, d.ex, ex, lx);
+    nonplane_elem<N>((int)r1, d.ey, ey, ly);
+    return (ex + sy * ey + sz * (int64_t)t) * N3 + lx + N * ly + N2 * N1;
+}
+
+template <int N>
+__device__ __forceinline__ int64_t edge_first(int q, const DsCat &d, int &kind) {
+    constexpr int N1 = N - 1, N2 = N * N;
+    constexpr int64_t N3 = (int64_t)N * N * N;
+    const int64_t sy = d.ex, sz = (int64_t)d.ex * d.ey;
+    unsigned t, r0, r1;
+    int ex, ey, ez, lx, ly, lz;
+    if (q < d.o[4]) {
+        kind = 0;
+        divmod((unsigned)(q - d.o[3]), d.fNZp, t, r0);
+        divmod(t, d.fEx1, t, r1);
+        nonplane_elem<N>((int)r0, d.ez, ez, lz);
+        return ((int64_t)r1 + sy * (int64_t)t + sz * ez) * N3 + N1 + N * N1 + N2 * lz;
+    }
+    if (q < d.o[5]) {
+        kind = 1;
+        divmod((unsigned)(q - d.o[4]), d.fNYp, t, r0);
+        divmod(t, d.fEx1, t, r1);
+        nonplane_elem<N>((int)r0, d.ey, ey, ly);
+        return ((int64_t)r1 + sy * ey + sz * (int64_t)t) * N3 + N1 + N * ly + N2 * N1;
+    }
+    kind = 2;
+    divmod((unsigned)(q - d.o[5]), d.fNXp, t, r0);
+    divmod(t, d.fEy1, t, r1);
+    nonplane_elem<N>((int)r0, d.ex, ex, lx);
+    return (ex + sy * (int64_t)r1 + sz * (int64_t)t) * N3 + lx + N * N1 + N2 * N1;
+}
+
+template <int N>
+__device__ __forceinline__ int64_t vertex_first(int q, const DsCat &d) {
+    constexpr int N1 = N - 1, N2 = N * N;
+    constexpr int64_t N3 = (int64_t)N * N * N;
+    const int64_t sy = d.ex, sz = (int64_t)d.ex * d.ey;
+    unsigned t, r0, r1;
+    divmod((unsigned)(q - d.o[6]), d.fEx1, t, r0);
+    divmod(t, d.fEy1, t, r1);
+    return ((int64_t)r0 + sy * (int64_t)r1 + sz * (int64_t)t) * N3 + N1 + N * N1 + N2 * N1;
+}
+
+// Offset of copy k (ascending element order, k < C) from the first copy of a
+// node with C copies (2 face, 4 edge, 8 vertex) of the given kind.  The
+// first copy sits at local coordinate N-1 along every interface direction,
+// copy k's element is one step further along the directions k selects and
+// its local coordinate there is 0.
+template <int N, int C>
+__device__ __forceinline__ int64_t copy_offset(int k, int kind, const DsCat &d) {
+    constexpr int N1 = N - 1, N2 = N * N;
+    constexpr int64_t N3 = (int64_t)N * N * N;
+    const int64_t sy = d.ex, sz = (int64_t)d.ex * d.ey;
+    const int64_t ox = N3 - N1, oy = sy * N3 - N * N1, oz = sz * N3 - N2 * N1;
+    if constexpr (C == 2) {
+        return kind == 0 ? ox : kind == 1 ? oy : oz;
+    } else if constexpr (C == 4) {
+        const int64_t o1 = kind == 2 ? oy : ox, o2 = kind == 0 ? oy : oz;
+        return ((k & 1) ? o1 : 0) + ((k & 2) ? o2 : 0);
+    } else {
+        return ((k & 1) ? ox : 0) + ((k & 2) ? oy : 0) + ((k & 4) ? oz : 0);
+    }
+}
+
 }  // namespace nekgb
