@@ -436,6 +436,25 @@ nb_status nb_axpby(nb_ctx *ctx, double alpha, const double *x_dev, double beta,
  * scratch buffer and a private stream; synchronous. */
 nb_status nb_fp32_rate(double *ffma_per_s);
 
+/* Measurement probe (not used by the solvers): the forward half of ax_e
+ * (Listing 1, Sec. III), w_e = D_r u_e + D_s u_e + D_t u_e for every
+ * element of the context, in FP64-level accuracy, computed by
+ *   method 0: the CG head's double-float even-odd line products on the
+ *             FP32 pipes;
+ *   method 1: the tensor cores (tcgen05 kind::f16, FP32 accumulation in
+ *             tensor memory) on an error-free split of u and D into six
+ *             balanced base-512 digits each (Ozaki et al. 2012), one chain
+ *             of n/2 MMAs (M = 128 lines, N = K = 8n) per direction and
+ *             element, the exact class sums recombined into float pairs.
+ * u_dev, w_dev: [E][n^3] FP64 on the device (r fastest); umax: an upper
+ * bound on max|u| (> 0).  n must be 8 or 10 (NB_ERR_ARG otherwise).  The
+ * kernel is timed as NB_K_AX when timing is on.  Allocates and frees a
+ * 13 KB digit image and a status word; synchronous.  NB_ERR_TIMEOUT if an
+ * MMA did not complete within about 1 s (its CTA then frees its tensor
+ * memory and stops). */
+nb_status nb_probe_grad(nb_ctx *ctx, int method, const double *u_dev, double *w_dev,
+                        double umax);
+
 /* --------------------------------------------------------------------- */
 /* Status                                                                */
 /* --------------------------------------------------------------------- */

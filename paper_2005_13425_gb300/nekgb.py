@@ -108,6 +108,7 @@ _SIGS = {
     "nb_slab_set_top": [_vp, _vp, _vp],
     "nb_slab_dot": [_vp, _vp, _vp, _dp],
     "nb_axpby": [_vp, ctypes.c_double, _vp, ctypes.c_double, _vp],
+    "nb_probe_grad": [_vp, ctypes.c_int, _vp, _vp, ctypes.c_double],
 }
 
 
@@ -341,6 +342,14 @@ def nb_timing_read(ctx, kernel_id: int, reset: bool = False):
     _check(load().nb_timing_read(ctx, int(kernel_id), ctypes.byref(ms), ctypes.byref(cnt),
                                  1 if reset else 0), "nb_timing_read")
     return ms.value, cnt.value
+
+
+def nb_probe_grad(ctx, method: int, u, w, umax: float):
+    """Measurement probe: w = D_r u + D_s u + D_t u per element, by the
+    double-float line products (method 0) or the tensor-core digit split
+    (method 1); see nekgb.h."""
+    _check(load().nb_probe_grad(ctx, int(method), _ptr(u, "torch.float64"), _ptr(w, "torch.float64"),
+                                float(umax)), "nb_probe_grad")
 
 
 def nb_fp32_rate() -> float:
