@@ -445,9 +445,13 @@ nb_status nb_fp32_rate(double *ffma_per_s);
  *             tensor memory) on an error-free split of u and D into six
  *             balanced base-512 digits each (Ozaki et al. 2012), one chain
  *             of n/2 MMAs (M = 128 lines, N = K = 8n) per direction and
- *             element, the exact class sums recombined into float pairs.
+ *             element, the exact class sums recombined into float pairs;
+ *             the three directions one after another;
+ *   method 2: as method 1 with the three directions' MMAs issued together
+ *             (three operand buffers and accumulators per CTA).
  * u_dev, w_dev: [E][n^3] FP64 on the device (r fastest); umax: an upper
- * bound on max|u| (> 0).  n must be 8 or 10 (NB_ERR_ARG otherwise).  The
+ * bound on max|u| (> 0).  n must be 8 or 10 and method 0, 1 or 2 (NB_ERR_ARG
+ * otherwise).  The
  * kernel is timed as NB_K_AX when timing is on.  Allocates and frees a
  * 13 KB digit image and a status word; synchronous.  NB_ERR_TIMEOUT if an
  * MMA did not complete within about 1 s (its CTA then frees its tensor

@@ -40,6 +40,11 @@ __device__ __forceinline__ void tmem_alloc(unsigned *dst, unsigned ncols) {
                  "r"(ncols)
                  : "memory");
 }
+// After its one allocation a CTA gives up the right to allocate, so that
+// further CTAs can be scheduled onto the SM while it runs.
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tmem_dealloc(unsigned taddr, unsigned ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
@@ -88,20 +93,25 @@ __host__ __device__ constexpr unsigned umma_idesc_f16(int M, int N) {
     return (1u << 4) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
 }
 
-template <int N>
+// NA = directions staged at once (1: one after another, 3: all together).
+template <int N, int NA = 1>
 struct TcLayout {
     static constexpr int M = 128;              // MMA rows: the n^2 lines of a direction, padded
     static constexpr int K = 8 * N;            // n points x 8 digit slots
     static constexpr int NOUT = 8 * N;         // n outputs x 8 classes
     static constexpr int LBO_A = 144;          // 128-byte core + 16 bytes: no bank conflicts on the stores
     static constexpr int SBO_A = N * LBO_A;
-    static constexpr int A_BYTES = (M / 8) * SBO_A;
+    static constexpr int A_BYTES = (M / 8) * SBO_A;   // one direction's A
+    static constexpr int A_ALL = NA * A_BYTES;
     static constexpr int LBO_B = 128;
     static constexpr int SBO_B = N * LBO_B;
     static constexpr int B_BYTES = N * SBO_B;
-    static constexpr int F_BYTES = 3 * N * N * N * 8;   // three directions' output pairs
-    static constexpr int SMEM = A_BYTES + B_BYTES + F_BYTES;
-    static constexpr unsigned TMEM_COLS = NOUT <= 32 ? 32 : (NOUT <= 64 ? 64 : 128);
+    // output pairs: one array that the directions, taken one after another,
+    // add into (NA = 1), or one per direction
+    static constexpr int F_BYTES = (NA == 1 ? 1 : 3) * N * N * N * 8;
+    static constexpr int SMEM = A_ALL + B_BYTES + F_BYTES;
+    static constexpr int COLS = NA * NOUT;
+    static constexpr unsigned TMEM_COLS = COLS <= 32 ? 32 : (COLS <= 64 ? 64 : (COLS <= 128 ? 128 : 256));
 };
 
 // Six balanced base-512 digits of h + l (|h + l| <= 1): h + l = sum_a
@@ -135,7 +145,7 @@ __device__ __forceinline__ uint4 digits6(float h, float l) {
 
 // The pair sc sum_q S_q 2^(-9q) (S_q exact integers in FP32, sc = 2^(1 + ED
 // - 18) for inputs <= 1 and |D| <= 2^(ED-1)): the two leading classes by
-// TwoSum, classes 3..6 by a plain sum below them.
+// TwoSum, classes 3..6 by a plain sum below them; unnormalised.
 __device__ __forceinline__ float2 recombine(const unsigned (&r)[8], float sc) {
     float v[8];
 #pragma unroll
@@ -146,9 +156,8 @@ __device__ __forceinline__ float2 recombine(const unsigned (&r)[8], float sc) {
     const float tail =
         __fmaf_rn(v[6], 0x1p-54f, __fmaf_rn(v[5], 0x1p-45f, __fmaf_rn(v[4], 0x1p-36f, __fmul_rn(v[3], 0x1p-27f))));
     const float e = __fadd_rn(e1, __fadd_rn(e2, tail));
-    const float hh = __fadd_rn(s, e);
-    const float ll = __fsub_rn(e, __fsub_rn(hh, s));
-    return make_float2(__fmul_rn(hh, sc), __fmul_rn(ll, sc));
+    // unnormalised (|e| within a few ulps of s), as the line products leave theirs
+    return make_float2(__fmul_rn(s, sc), __fmul_rn(e, sc));
 }
 
 struct ProbeArgs {
@@ -161,10 +170,13 @@ struct ProbeArgs {
     int *status;          // set to NB_ERR_TIMEOUT if an MMA does not complete
 };
 
+// METHOD 0: line products; 1: tensor cores, one direction at a time; 2:
+// tensor cores, the three directions' MMAs issued together.
 template <int N, int METHOD>
 __global__ void __launch_bounds__(kProbeThreads)
 probe_grad_kernel(ProbeArgs a, const __grid_constant__ EoMat<N> Dm) {
-    using L = TcLayout<N>;
+    constexpr int NA = METHOD == 2 ? 3 : 1;
+    using L = TcLayout<N, NA>;
     constexpr int N2 = N * N, N3 = N * N * N;
     constexpr int T = kProbeThreads;
     constexpr int PPT = (N3 + T - 1) / T;
@@ -173,27 +185,47 @@ probe_grad_kernel(ProbeArgs a, const __grid_constant__ EoMat<N> Dm) {
     __shared__ unsigned s_tmem;
     const int t = threadIdx.x;
     // [3][N3] output pairs; method 0 keeps its input pairs X in front of them
-    float2 *F = reinterpret_cast<float2 *>(psm + (METHOD == 1 ? L::A_BYTES + L::B_BYTES : N3 * 8));
+    float2 *F = reinterpret_cast<float2 *>(psm + (METHOD >= 1 ? L::A_ALL + L::B_BYTES : N3 * 8));
     float2 *X = reinterpret_cast<float2 *>(psm);
     unsigned tbase = 0;
-    if constexpr (METHOD == 1) {
+    if constexpr (METHOD >= 1) {
         if (t == 0) {
             mbar_init(&bar, 1);
             fence_mbar_init();
         }
-        if (t < 32) tmem_alloc(&s_tmem, L::TMEM_COLS);
+        if (t < 32) {
+            tmem_alloc(&s_tmem, L::TMEM_COLS);
+            tmem_relinquish();
+        }
         for (int q = t; q < L::B_BYTES / 16; q += T)
-            reinterpret_cast<uint4 *>(psm + L::A_BYTES)[q] = a.bimg[q];
+            reinterpret_cast<uint4 *>(psm + L::A_ALL)[q] = a.bimg[q];
         fence_proxy_async();
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
         tbase = s_tmem;
     }
-    const unsigned a_addr = smem_addr(psm), b_addr = smem_addr(psm + L::A_BYTES);
+    const unsigned a_addr = smem_addr(psm), b_addr = smem_addr(psm + L::A_ALL);
     constexpr unsigned IDESC = umma_idesc_f16(L::M, L::NOUT);
     unsigned phase = 0;
     bool ok = true;
+    // A offsets of this thread's points in each direction's layout (row =
+    // line, core = position along the line) and the bases of its output
+    // points: the same for every element
+    int aoff[PPT][3];
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        const int q = t + k * T;
+        const int pi = q % N, pj = (q / N) % N, pk = q / N2;
+        const int ln[3] = {pj + N * pk, pi + N * pk, pi + N * pj}, pos[3] = {pi, pj, pk};
+#pragma unroll
+        for (int d = 0; d < 3; d++) aoff[k][d] = (ln[d] >> 3) * L::SBO_A + pos[d] * L::LBO_A + (ln[d] & 7) * 16;
+    }
+    const int wq = t >> 5, line = 32 * (wq & 3) + (t & 31);   // this thread's TMEM lane
+    const int i0 = (wq >> 2) * (N / 2);                        // its outputs i0 .. i0 + N/2 - 1
+    // output point of (line, i) in direction d: obase[d] + i * ostep[d]
+    const int obase[3] = {N * line, (line % N) + N2 * (line / N), line};
+    constexpr int ostep[3] = {1, N, N2};
     for (int64_t e = blockIdx.x; e < a.E && ok; e += gridDim.x) {
         const double *u = a.u + e * N3;
         if constexpr (METHOD == 0) {
@@ -215,59 +247,64 @@ probe_grad_kernel(ProbeArgs a, const __grid_constant__ EoMat<N> Dm) {
                     dg[k] = digits6(v.x, v.y);
                 }
             }
-            const int w = t >> 5, lane = t & 31;
-            const int line = 32 * (w & 3) + lane;           // this thread's TMEM lane
-            const int i0 = (w >> 2) * (N / 2);              // its outputs i0 .. i0 + N/2 - 1
-#pragma unroll 1
-            for (int dir = 0; dir < 3; dir++) {
-                // this direction's A: row = line, core = position along the line
+            const unsigned lrow = (unsigned)(32 * (wq & 3)) << 16;
 #pragma unroll
-                for (int k = 0; k < PPT; k++) {
-                    const int q = t + k * T;
-                    if (q < N3) {
-                        const int pi = q % N, pj = (q / N) % N, pk = q / N2;
-                        const int ln = dir == 0 ? pj + N * pk : (dir == 1 ? pi + N * pk : pi + N * pj);
-                        const int pos = dir == 0 ? pi : (dir == 1 ? pj : pk);
-                        *reinterpret_cast<uint4 *>(psm + (ln >> 3) * L::SBO_A + pos * L::LBO_A + (ln & 7) * 16) =
-                            dg[k];
-                    }
+            for (int d0 = 0; d0 < 3; d0 += NA) {
+#pragma unroll
+                for (int dd = 0; dd < NA; dd++) {
+#pragma unroll
+                    for (int k = 0; k < PPT; k++)
+                        if (t + k * T < N3)
+                            *reinterpret_cast<uint4 *>(psm + dd * L::A_BYTES + aoff[k][d0 + dd]) = dg[k];
                 }
                 fence_proxy_async();
                 tc_fence_before();
                 __syncthreads();
                 tc_fence_after();
+                bool done = true;
                 if (t == 0) {
 #pragma unroll
-                    for (int ks = 0; ks < N / 2; ks++)
-                        tc_mma_f16(tbase, umma_desc(a_addr + ks * 2 * L::LBO_A, L::LBO_A, L::SBO_A),
-                                   umma_desc(b_addr + ks * 2 * L::LBO_B, L::LBO_B, L::SBO_B), IDESC, ks > 0);
+                    for (int dd = 0; dd < NA; dd++)
+#pragma unroll
+                        for (int ks = 0; ks < N / 2; ks++)
+                            tc_mma_f16(tbase + dd * L::NOUT,
+                                       umma_desc(a_addr + dd * L::A_BYTES + ks * 2 * L::LBO_A, L::LBO_A, L::SBO_A),
+                                       umma_desc(b_addr + ks * 2 * L::LBO_B, L::LBO_B, L::SBO_B), IDESC, ks > 0);
                     tc_commit(&bar);
+                    // one thread observes completion; the barrier and the
+                    // fence after it order the others' TMEM loads behind it
+                    done = mbar_wait(&bar, phase);
                 }
-                const bool done = mbar_wait(&bar, phase);
+                tc_fence_before();
                 if (!__syncthreads_and(done)) {
                     ok = false;
                     break;
                 }
-                phase ^= 1u;
                 tc_fence_after();
-                const unsigned lrow = (unsigned)(32 * (w & 3)) << 16;
-                // this thread's outputs, TB at a time: TMEM loads, one wait, recombination
-                constexpr int TB = 2;
+                phase ^= 1u;
 #pragma unroll
-                for (int o0 = 0; o0 < N / 2; o0 += TB) {
-                    unsigned r[TB][8];
+                for (int dd = 0; dd < NA; dd++) {
+                    const int dir = d0 + dd;
+                    // this thread's outputs, TB at a time: TMEM loads, one wait, recombination
+                    constexpr int TB = 2;
 #pragma unroll
-                    for (int o = 0; o < TB; o++)
-                        if (o0 + o < N / 2) tc_ld8(tbase + lrow + 8 * (i0 + o0 + o), r[o]);
-                    tc_wait_ld();
-                    if (line < N2) {
+                    for (int o0 = 0; o0 < N / 2; o0 += TB) {
+                        unsigned r[TB][8];
 #pragma unroll
-                        for (int o = 0; o < TB; o++) {
-                            if (o0 + o >= N / 2) break;
-                            const int i = i0 + o0 + o;
-                            const int P = dir == 0 ? i + N * line
-                                                   : (dir == 1 ? (line % N) + N * i + N2 * (line / N) : line + N2 * i);
-                            F[dir * N3 + P] = recombine(r[o], a.rscale);
+                        for (int o = 0; o < TB; o++)
+                            if (o0 + o < N / 2) tc_ld8(tbase + lrow + dd * L::NOUT + 8 * (i0 + o0 + o), r[o]);
+                        tc_wait_ld();
+                        if (line < N2) {
+#pragma unroll
+                            for (int o = 0; o < TB; o++) {
+                                if (o0 + o >= N / 2) break;
+                                const float2 v = recombine(r[o], a.rscale);
+                                const int P = obase[dir] + (i0 + o0 + o) * ostep[dir];
+                                if (NA == 1)   // directions in turn: add into the one array
+                                    F[P] = dir == 0 ? v : dfa::add(F[P], v);
+                                else
+                                    F[dir * N3 + P] = v;
+                            }
                         }
                     }
                 }
@@ -277,11 +314,13 @@ probe_grad_kernel(ProbeArgs a, const __grid_constant__ EoMat<N> Dm) {
             __syncthreads();
         }
         double *w = a.w + e * N3;
-        for (int q = t; q < N3; q += T)
-            __stcs(w + q, dfa::join_scaled(dfa::add(dfa::add(F[q], F[N3 + q]), F[2 * N3 + q]), -a.sh));
+        for (int q = t; q < N3; q += T) {
+            const float2 v = METHOD == 1 ? F[q] : dfa::add(dfa::add(F[q], F[N3 + q]), F[2 * N3 + q]);
+            __stcs(w + q, dfa::join_scaled(v, -a.sh));
+        }
         __syncthreads();
     }
-    if constexpr (METHOD == 1) {
+    if constexpr (METHOD >= 1) {
         if (!ok) {   // an MMA did not complete in time: wait once more (bounded), then free TMEM
             if (t == 0) {
                 mbar_wait(&bar, phase);
@@ -328,8 +367,8 @@ static std::vector<uint16_t> b_image(const double *Dm, int ED) {
 
 template <int N, int METHOD>
 static nb_status probe_launch(nb_ctx *c, const double *u, double *w, int sh) {
-    using L = TcLayout<N>;
-    const size_t smem = METHOD == 1 ? (size_t)L::SMEM : (size_t)(N * N * N * 8 + L::F_BYTES);
+    using L = TcLayout<N, METHOD == 2 ? 3 : 1>;
+    const size_t smem = METHOD >= 1 ? (size_t)L::SMEM : (size_t)(N * N * N * 8 * 4);   // method 0: X + 3 arrays
     EoMat<N> Dm;
     eo_consts<N>(c->D_host, false, Dm);
     ProbeArgs a{};
@@ -347,7 +386,7 @@ static nb_status probe_launch(nb_ctx *c, const double *u, double *w, int sh) {
             break;
         }
         a.status = d_status;
-        if (METHOD == 1) {
+        if (METHOD >= 1) {
             double dmax = 0.0;
             for (int q = 0; q < N * N; q++) dmax = fmax(dmax, fabs(c->D_host[q]));
             const int ED = (int)ceil(log2(dmax)) + 1;   // |D| 2^-ED <= 1/2
@@ -367,7 +406,20 @@ static nb_status probe_launch(nb_ctx *c, const double *u, double *w, int sh) {
         if ((st = set_smem(kern, smem)) != NB_OK) break;
         int occ = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kProbeThreads, smem);
-        if (METHOD == 1 && occ * (int)L::TMEM_COLS > 512) occ = 512 / (int)L::TMEM_COLS;
+        if (METHOD >= 1) {
+            // the occupancy query answers 1 for this kernel; take the limits
+            // of shared memory, registers and tensor memory (512 columns)
+            cudaFuncAttributes fa{};
+            if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
+                st = cuda_fail(cudaGetLastError(), "cudaFuncGetAttributes");
+                break;
+            }
+            const int by_smem = (227 * 1024) / ((int)smem + (int)fa.sharedSizeBytes + 1024);
+            const int by_regs = 65536 / (((fa.numRegs + 7) / 8) * 8 * kProbeThreads);
+            const int by_tmem = 512 / (int)L::TMEM_COLS;
+            occ = by_smem < by_regs ? by_smem : by_regs;
+            occ = occ < by_tmem ? occ : by_tmem;
+        }
         if (occ < 1) occ = 1;
         const int64_t cap = (int64_t)device_sms() * occ;
         const int grid = (int)(c->m.E < cap ? c->m.E : cap);
@@ -402,11 +454,16 @@ extern "C" nb_status nb_probe_grad(nb_ctx *c, int method, const double *u, doubl
     try {
         if (!c) return fail(NB_ERR_ARG, "NULL context");
         if (!u || !w || !(umax > 0.0) || !isfinite(umax)) return fail(NB_ERR_ARG, "nb_probe_grad: bad arguments");
-        if (method != 0 && method != 1) return fail(NB_ERR_ARG, "nb_probe_grad: method is 0 or 1");
+        if (method < 0 || method > 2) return fail(NB_ERR_ARG, "nb_probe_grad: method is 0, 1 or 2");
         const int sh = -(int)ceil(log2(umax));   // |u| 2^sh <= 1
         switch (c->m.n) {
-            case 8: return method == 0 ? probe_launch<8, 0>(c, u, w, sh) : probe_launch<8, 1>(c, u, w, sh);
-            case 10: return method == 0 ? probe_launch<10, 0>(c, u, w, sh) : probe_launch<10, 1>(c, u, w, sh);
+            case 8:
+                return method == 0 ? probe_launch<8, 0>(c, u, w, sh)
+                                   : (method == 1 ? probe_launch<8, 1>(c, u, w, sh) : probe_launch<8, 2>(c, u, w, sh));
+            case 10:
+                return method == 0 ? probe_launch<10, 0>(c, u, w, sh)
+                                   : (method == 1 ? probe_launch<10, 1>(c, u, w, sh)
+                                                  : probe_launch<10, 2>(c, u, w, sh));
             default: return fail(NB_ERR_ARG, "nb_probe_grad: n must be 8 or 10");
         }
     } catch (const std::bad_alloc &) {

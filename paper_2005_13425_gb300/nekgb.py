@@ -347,7 +347,7 @@ def nb_timing_read(ctx, kernel_id: int, reset: bool = False):
 def nb_probe_grad(ctx, method: int, u, w, umax: float):
     """Measurement probe: w = D_r u + D_s u + D_t u per element, by the
     double-float line products (method 0) or the tensor-core digit split
-    (method 1); see nekgb.h."""
+    (methods 1 and 2); see nekgb.h."""
     _check(load().nb_probe_grad(ctx, int(method), _ptr(u, "torch.float64"), _ptr(w, "torch.float64"),
                                 float(umax)), "nb_probe_grad")
 

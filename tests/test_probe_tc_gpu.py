@@ -2,7 +2,8 @@
 
 w_e = D_r u_e + D_s u_e + D_t u_e (the forward half of ax_e, Listing 1) by
 the double-float line products (method 0) and by tcgen05 MMAs on a
-base-512 digit split of u and D (method 1), compared element by element
+base-512 digit split of u and D (methods 1 and 2: the directions one after
+another or together), compared element by element
 with the same sum formed in FP64 by numpy from the device's own D.  Both
 must meet the 1e-12 max-norm relative bound of the FP64 operator; the
 digit split is exact in its class sums, so any loss of bits in the tensor
@@ -50,7 +51,7 @@ def test_probe_methods_match_fp64(nek, dims, n, scale):
         want = fp64_grad_sum(D, u, n)
         ud = torch.from_numpy(u).cuda()
         umax = float(np.abs(u).max())
-        for method in (0, 1):
+        for method in (0, 1, 2):
             w = torch.full_like(ud, float("nan"))
             nek.nb_probe_grad(ctx, method, ud, w, umax)
             stream.synchronize()
