@@ -372,9 +372,19 @@ typedef enum {
     NB_K_COUNT = 6
 } nb_kernel_id;
 
-/* on != 0: record an event pair around every kernel launch (CUDA graphs
- * are not used while timing is on); off: release the records. */
+/* on = 1: record an event pair around every kernel launch (CUDA graphs
+ * are not used while timing is on).  on = 2 (sampled): the same, except in
+ * the FP64 CG solve, which keeps its CUDA graphs and runs the first
+ * iteration of every chunk of 16 as event-timed plain launches and the other
+ * 15 as a graph, so that timing barely changes the solve's own speed.
+ * on = 0: off.  Each call resets the accumulated times and the launch count
+ * (nb_launch_count).  NB_ERR_ARG for other values of on. */
 nb_status nb_timing_enable(nb_ctx *ctx, int on);
+
+/* Kernels of the library launched on the context's stream since timing was
+ * last enabled or disabled (nb_timing_enable), timed or not; a graph launch
+ * counts the kernels the graph holds. */
+nb_status nb_launch_count(nb_ctx *ctx, int64_t *launched);
 
 /* Accumulated device time (ms) and launch count per kernel class since
  * timing was enabled or last reset (synchronises the stream). */

@@ -67,6 +67,11 @@ cudaError_t dev_alloc(void **p, size_t bytes) {
 }
 
 LaunchTimer::LaunchTimer(nb_ctx *ctx, int k) : c(ctx), kid(k) {
+    if (c->capturing) {   // counted when the graph is launched
+        c->capture_count++;
+        return;
+    }
+    c->n_launched++;
     if (!c->timing) return;
     if (c->event_pool.size() < 2) {
         for (int q = 0; q < 64; q++) {
@@ -519,10 +524,20 @@ nb_status nb_set_ax_variant(nb_ctx *c, int v) {
 nb_status nb_timing_enable(nb_ctx *c, int on) {
     NB_GUARD_BEGIN
     if (!c) return fail(NB_ERR_ARG, "NULL context");
+    if (on < 0 || on > 2) return fail(NB_ERR_ARG, "nb_timing_enable: on is 0, 1 or 2");
     nb_status s = harvest_timing(c);
-    c->timing = on != 0;
+    c->timing = on;
+    c->n_launched = 0;
     for (int k = 0; k < NB_K_COUNT; k++) { c->t_ms[k] = 0; c->t_launch[k] = 0; }
     return s;
+    NB_GUARD_END
+}
+
+nb_status nb_launch_count(nb_ctx *c, int64_t *launched) {
+    NB_GUARD_BEGIN
+    if (!c || !launched) return fail(NB_ERR_ARG, "nb_launch_count: NULL argument");
+    *launched = c->n_launched;
+    return NB_OK;
     NB_GUARD_END
 }
 

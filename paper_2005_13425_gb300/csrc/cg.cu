@@ -369,7 +369,10 @@ static nb_status build_graph(nb_ctx *c, int chunk) {
     cudaGraph_t g = nullptr;
     NB_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     nb_status s = NB_OK;
+    c->capturing = true;
+    c->capture_count = 0;
     for (int k = 0; k < chunk && s == NB_OK; k++) s = enqueue_iteration(c);
+    c->capturing = false;
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (s != NB_OK) {
         if (g) cudaGraphDestroy(g);
@@ -381,6 +384,7 @@ static nb_status build_graph(nb_ctx *c, int chunk) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     c->cg_graph_chunk = chunk;
     c->cg_graph_two = c->two_kernel;
+    c->cg_graph_kernels = c->capture_count;
     return NB_OK;
 }
 
@@ -404,15 +408,24 @@ nb_status cg_solve_fp64(nb_ctx *c, const double *f, double *x, double tol, int m
     if ((s = launch_mask_sc(c, c->d_w, nullptr)) != NB_OK) return s;
     if ((s = launch_dot(c, 2, f, c->d_w, nullptr)) != NB_OK) return s;
 
-    // Stream capture needs a non-default stream; timing needs plain launches.
-    const bool use_graph = c->stream != nullptr && !c->timing;
+    // Stream capture needs a non-default stream; event timing needs plain
+    // launches.  Sampled timing (timing = 2) runs the first iteration of
+    // every chunk as plain, event-timed launches and the rest as a graph.
+    const bool sampled = c->timing == 2;
+    const bool use_graph = c->stream != nullptr && (!c->timing || sampled);
     const int chunk = 16;
     int launched = 0;
     while (launched < maxit) {
         if (use_graph) {
-            if ((s = build_graph(c, chunk)) != NB_OK) return s;
+            if (sampled) {
+                if ((s = enqueue_iteration(c)) != NB_OK) return s;
+                launched += 1;
+            }
+            const int g = sampled ? chunk - 1 : chunk;
+            if ((s = build_graph(c, g)) != NB_OK) return s;
             NB_CUDA(cudaGraphLaunch(c->cg_graph, c->stream));
-            launched += chunk;
+            c->n_launched += c->cg_graph_kernels;
+            launched += g;
         } else {
             for (int k = 0; k < chunk && launched < maxit; k++, launched++)
                 if ((s = enqueue_iteration(c)) != NB_OK) return s;
@@ -424,7 +437,7 @@ nb_status cg_solve_fp64(nb_ctx *c, const double *f, double *x, double tol, int m
         }
     }
     {
-        LaunchTimer tm(c, NB_K_UPDATE);
+        LaunchTimer tm(c, NB_K_OTHER);
         const int grid = grid_blocks(c->m.npts, 256, sms() * 8);
         final_x_kernel<<<grid, 256, 0, c->stream>>>(c->d_x, c->d_p, c->m.npts, c->d_sc);
         NB_LAUNCH_CHECK("final_x_kernel");

@@ -155,8 +155,14 @@ struct nb_ctx {
     double mixed_inner_tol = 1e-4;
     int mixed_max_outer = 50;
     int last_outer = 0;
-    // timing
-    bool timing = false;
+    // timing: 0 off, 1 every launch event-timed (no graphs), 2 sampled (the
+    // FP64 CG keeps its graphs and event-times one iteration per chunk)
+    int timing = 0;
+    bool capturing = false;             // a graph is being captured: launches are counted into capture_count
+    int capture_count = 0;
+    int cg_graph_kernels = 0;           // kernels in cg_graph
+    int cg_graph32_kernels = 0;         // kernels in cg_graph32
+    int64_t n_launched = 0;             // kernels launched since timing was last enabled (graph kernels included)
     std::vector<nekgb::TimingRec> pending;
     std::vector<cudaEvent_t> event_pool;
     double t_ms[NB_K_COUNT] = {0};

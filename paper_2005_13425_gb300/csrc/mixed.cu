@@ -137,7 +137,10 @@ static nb_status build_graph32(nb_ctx *c, int chunk) {
     cudaGraph_t g = nullptr;
     NB_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     nb_status s = NB_OK;
+    c->capturing = true;
+    c->capture_count = 0;
     for (int k = 0; k < chunk && s == NB_OK; k++) s = inner_iteration(c);
+    c->capturing = false;
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (s != NB_OK) {
         if (g) cudaGraphDestroy(g);
@@ -148,6 +151,7 @@ static nb_status build_graph32(nb_ctx *c, int chunk) {
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     c->cg_graph32_chunk = chunk;
+    c->cg_graph32_kernels = c->capture_count;
     return NB_OK;
 }
 
@@ -222,6 +226,7 @@ nb_status cg_solve_mixed(nb_ctx *c, const double *f, double *x, double tol, int 
             if (use_graph) {
                 if ((s = build_graph32(c, chunk)) != NB_OK) return s;
                 NB_CUDA(cudaGraphLaunch(c->cg_graph32, c->stream));
+                c->n_launched += c->cg_graph32_kernels;
                 launched += chunk;
             } else {
                 for (int k = 0; k < chunk && launched < budget; k++, launched++)

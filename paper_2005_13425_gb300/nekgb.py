@@ -22,6 +22,7 @@ NB_OK, NB_ERR_ARG, NB_ERR_CUDA, NB_ERR_OOM = 0, 1, 2, 3
 NB_ERR_NOT_CONVERGED, NB_ERR_BREAKDOWN, NB_ERR_TIMEOUT, NB_ERR_STATE = 4, 5, 6, 7
 NB_FP64, NB_MIXED = 0, 1
 NB_K_AX, NB_K_DSSUM, NB_K_MASK, NB_K_DOT, NB_K_UPDATE, NB_K_OTHER = range(6)
+NB_K_COUNT = 6
 KERNEL_NAMES = {NB_K_AX: "ax_e", NB_K_DSSUM: "dssum", NB_K_MASK: "mask",
                 NB_K_DOT: "dot", NB_K_UPDATE: "update", NB_K_OTHER: "other"}
 
@@ -97,6 +98,7 @@ _SIGS = {
     "nb_engine_stats": [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t), _ip],
     "nb_engine_tuning": [_vp, ctypes.c_int, ctypes.c_int, _ip, _ip],
     "nb_timing_enable": [_vp, ctypes.c_int],
+    "nb_launch_count": [_vp, ctypes.POINTER(ctypes.c_int64)],
     "nb_timing_read": [_vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
     "nb_fp32_rate": [_dp],
     "nb_setup_slab": [ctypes.POINTER(_vp), nb_box, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -332,8 +334,15 @@ def nb_set_ax_variant(ctx, variant: int):
     _check(load().nb_set_ax_variant(ctx, int(variant)), "nb_set_ax_variant")
 
 
-def nb_timing_enable(ctx, on: bool):
-    _check(load().nb_timing_enable(ctx, 1 if on else 0), "nb_timing_enable")
+def nb_timing_enable(ctx, on):
+    """on: False/0 off, True/1 every launch event-timed, 2 sampled (see nekgb.h)."""
+    _check(load().nb_timing_enable(ctx, int(on)), "nb_timing_enable")
+
+
+def nb_launch_count(ctx) -> int:
+    n = ctypes.c_int64(0)
+    _check(load().nb_launch_count(ctx, ctypes.byref(n)), "nb_launch_count")
+    return n.value
 
 
 def nb_timing_read(ctx, kernel_id: int, reset: bool = False):

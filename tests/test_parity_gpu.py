@@ -535,6 +535,44 @@ def test_cg_host_buffers_and_timing(nek, oracle):
     assert cnt == 21 and ms > 0          # 20 iterations + the initial residual
 
 
+def test_sampled_timing_keeps_the_solve_and_counts_launches(nek, oracle):
+    """Sampled timing (nb_timing_enable(ctx, 2)) keeps the FP64 CG's graphs
+    and event-times the first iteration of each chunk of 16: the solution and
+    the rho history are bit-identical to an untimed solve, the timed launches
+    are one iteration per chunk plus the once-per-solve kernels, and
+    nb_launch_count counts every kernel, graph kernels included.  With every
+    launch timed (1) the solve runs exactly maxit iterations of plain launches."""
+    dims, n = (4, 3, 3), 10          # n = 10: the two-kernel iteration (head + assemble_update)
+    P, f = cg_inputs(oracle, dims, n)
+    maxit = 40                       # three chunks of 16 are launched; the last 8 iterations return at once
+    with Ctx(nek, dims, n, P["D"], P["gxyz"]) as ctx:
+        runs = {}
+        for mode in (0, 2, 1):
+            nek.nb_timing_enable(ctx, mode)
+            x = torch.zeros_like(dev(f))
+            st, it, rr = nek.nb_cg_solve(ctx, dev(f), x, tol=0.0, maxit=maxit)
+            timed = {k: nek.nb_timing_read(ctx, k)[1] for k in range(nek.NB_K_COUNT)}
+            runs[mode] = (host(x), nek.nb_cg_history(ctx), it, timed, nek.nb_launch_count(ctx))
+        nek.nb_timing_enable(ctx, 0)
+        with pytest.raises(nek.NekgbError) as ei:
+            nek.nb_timing_enable(ctx, 3)
+        assert ei.value.status == nek.NB_ERR_ARG
+    x0, h0, it0, _, _ = runs[0]
+    for mode in (1, 2):
+        xm, hm, itm, _, _ = runs[mode]
+        assert itm == it0 == maxit and np.array_equal(xm, x0) and np.array_equal(hm, h0)
+    # setup: ax_e (w = A x0), dssum, mask, dot; then the iterations; then final x (other)
+    _, _, _, t2, n2 = runs[2]
+    chunks = -(-maxit // 16)
+    assert n2 == 4 + 2 * 16 * chunks + 1
+    assert t2[nek.NB_K_AX] == 1 + chunks and t2[nek.NB_K_UPDATE] == chunks
+    assert t2[nek.NB_K_DSSUM] == 1 and t2[nek.NB_K_MASK] == 1 and t2[nek.NB_K_DOT] == 1
+    assert t2[nek.NB_K_OTHER] == 1
+    _, _, _, t1, n1 = runs[1]
+    assert n1 == 4 + 2 * maxit + 1 == sum(t1.values())
+    assert t1[nek.NB_K_AX] == 1 + maxit and t1[nek.NB_K_UPDATE] == maxit
+
+
 def test_argument_errors_on_device(nek):
     dims, n = (2, 2, 2), 4
     with Ctx(nek, dims, n, np.eye(n), np.zeros((8, 6, n ** 3))) as ctx:
