@@ -6,7 +6,10 @@ n = 10 GLL points per direction (degree 9), FP64-accurate: every iteration
 runs the ax_e head (x += alpha p, p = r + beta p, w = ax_e(p), mask,
 <w,p>_c, alpha) and the fused dssum + r update (<r,r>_c, beta).  The metric
 is Ax throughput in GDOF/s: local points (E n^3) times CG iterations,
-divided by the device time.  The working set (gxyz pairs 197 MB + four
+divided by the device time.  The solver runs as it does untimed, with CUDA
+graphs; per-kernel CUDA events are recorded around one CG iteration in 16
+(sampled timing), which gives the roofline's kernel time in the same
+region, and `gpu_launches` counts every kernel launched.  The working set (gxyz pairs 197 MB + four
 33 MB vectors) is larger than the 129 MB L2, so no flush is needed between
 iterations; the standalone ax_e timings below flush L2.
 
