@@ -1146,11 +1146,15 @@ nb_status engine_submit_internal(nb_engine *g, nb_box box, int n, double amp, co
 nb_status engine_retire_internal(nb_engine *g, int id, double *x);
 nb_status engine_step_internal(nb_engine *g, int iters);
 
-// Time the CG iteration of a synthetic 8x8x8-element problem for each
-// candidate (lines per thread, elements per tile): the median of five
-// 24-iteration runs.  The default layout (one line per thread, 8 elements
-// per tile) is kept unless a candidate is at least 2 % faster, so that run-
-// to-run noise does not flip the choice.
+// Time the CG iteration of a synthetic problem for each candidate (lines
+// per thread, elements per tile): the median of five 24-iteration runs.
+// The problem is a cube of about 128 elements per SM, so that even the
+// largest tiles give every resident CTA at least two (a smaller problem
+// leaves CTAs idle and favours the smallest tiles, whatever a large batch
+// would want).  The default layout (one line per thread, 8 elements per
+// tile) is kept unless a candidate is at least 2 % faster, so that run-to-
+// run noise does not flip the choice; an arena without room for the problem
+// keeps the defaults.
 static nb_status autotune(nb_engine *g, int n, int prec) {
     const bool mixed = prec == NB_MIXED;
     NGroup &G = mixed ? g->mgroups[n] : g->groups[n];
@@ -1176,7 +1180,9 @@ static nb_status autotune(nb_engine *g, int n, int prec) {
     float best = 1e30f, dflt = 1e30f;
     const int dl = !mixed && n >= 13 ? 2 : 1, dt = 8;
     int bl = dl, bt = dt;
-    const nb_box box = {8, 8, 8};
+    int side = 8;
+    while (side * side * side < 128 * prop.multiProcessorCount) side++;
+    const nb_box box = {side, side, side};
     const Mesh m = make_mesh(box, n);
     double *f = nullptr;
     cudaError_t e = dev_alloc((void **)&f, sizeof(double) * m.npts);
