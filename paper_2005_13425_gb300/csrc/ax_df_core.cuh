@@ -56,7 +56,8 @@ __host__ __device__ constexpr int df_threads_lpt(int n, int lpt) {
 // element operator asks for: as many as the six n^3 pair arrays allow in
 // 228 KB of shared memory (1 KB reserved per CTA), but no more than leave R
 // registers per thread (a line at n <= 10 needs 48; the batched kernel's
-// tile bookkeeping needs more); 4 at n = 10, 2 at n = 11, 12 for R = 48.
+// tile head then spills about 100 bytes at n = 10, which costs less than
+// the CTA a 64-register bound loses); 4 at n = 10, 2 at n = 11, 12 for R = 48.
 // Above n = 12 a line's registers cannot be bounded without spilling.
 template <int N, int T, int R = 48>
 __host__ __device__ constexpr int df_min_blocks() {

@@ -182,7 +182,7 @@ __device__ __forceinline__ double eng_head_tile(const ProbDesc &P, int64_t e0, i
 
 // CG head over a list of (slot, tile) work units.
 template <int N, int T>
-__global__ void __launch_bounds__(T, df_min_blocks<N, T, 64>())
+__global__ void __launch_bounds__(T, df_min_blocks<N, T, 48>())
 eng_ax_head(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles,
             const __grid_constant__ DfEo<N> D) {
     extern __shared__ float2 sm[];
@@ -1079,36 +1079,6 @@ static nb_status dispatch_mixed(nb_engine *g, int n, bool outer) {
     return fail(NB_ERR_ARG, "unsupported n");
 }
 
-// True when the CG head for (n, lines per thread) uses local memory
-// (register spills); the autotuner skips such variants when the other one
-// does not spill.
-template <int N, int LPT>
-static bool head_spills_nl() {
-    constexpr int T = df_threads_lpt(N, LPT);
-    cudaFuncAttributes at{};
-    if (cudaFuncGetAttributes(&at, eng_ax_head<N, T>) != cudaSuccess) return false;
-    return at.localSizeBytes > 0;
-}
-
-static bool head_spills(int n, int lpt) {
-    bool s1 = false, s2 = false;
-    switch (n) {
-#define NB_CASE(NN)                                                          \
-    case NN:                                                                 \
-        if constexpr (NN < 13) s1 = head_spills_nl<NN, 1>();                 \
-        s2 = head_spills_nl<NN, 2>();                                        \
-        break;
-        NB_CASE(2) NB_CASE(3) NB_CASE(4) NB_CASE(5) NB_CASE(6) NB_CASE(7) NB_CASE(8)
-        NB_CASE(9) NB_CASE(10) NB_CASE(11) NB_CASE(12) NB_CASE(13) NB_CASE(14) NB_CASE(15)
-        NB_CASE(16)
-#undef NB_CASE
-        default: break;
-    }
-    if (n >= 13) return false;               // only the two-line variant exists
-    if (s1 == s2) return false;              // both or neither spill: let the timing decide
-    return lpt == 1 ? s1 : s2;
-}
-
 // ---- autotuner: lines per thread and elements per tile, per n
 static std::mutex g_tune_mu;
 
@@ -1196,7 +1166,6 @@ static nb_status autotune(nb_engine *g, int n, int prec) {
     for (int li = 0; li < 2 && st == NB_OK; li++) {
         if (mixed && li == 1) break;              // the FP32 head has one thread layout (lines per thread 1)
         if (!mixed && n >= 13 && lpts[li] == 1) continue;
-        if (!mixed && head_spills(n, lpts[li])) continue;   // a variant that spills is never the fastest
         for (int ti = 0; ti < 3 && st == NB_OK; ti++) {
             G.lpt = lpts[li];
             if (g->graph) {   // captured with another candidate's kernels
