@@ -183,18 +183,31 @@ __device__ __forceinline__ double eng_head_tile(const ProbDesc &P, int64_t e0, i
 // CG head over a list of (slot, tile) work units.
 template <int N, int T>
 __global__ void __launch_bounds__(T, df_min_blocks<N, T, 48>())
-eng_ax_head(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const int *__restrict__ ntiles,
+eng_ax_head(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, int *__restrict__ ntiles,
             const __grid_constant__ DfEo<N> D) {
     extern __shared__ float2 sm[];
     __shared__ int s_last;
     __shared__ double red[32];
     unsigned pf[df_points_per_thread<N, T>()];
     df_point_masks<N, T>(pf);
-    const int nt = *ntiles;
-    for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    // Tiles after the first come from a counter (ntiles[2]), so that SMs
+    // that run slower take fewer; a tile's result does not depend on the CTA
+    // that computes it.  Thread 0 takes the next index at the start of a
+    // tile into one of two slots (alternating, so that no thread can still be
+    // reading a slot when it is written again) and the CTA reads it after the
+    // tile's barriers; the last CTA to leave resets the counter for the next
+    // launch (ntiles[3] counts them).
+    __shared__ int s_next[2];
+    const int nt = ntiles[0];
+    int par = 0;
+    for (int ti = blockIdx.x; ti < nt; ti = s_next[par], par ^= 1) {
+        if (threadIdx.x == 0) s_next[par] = (int)gridDim.x + atomicAdd(ntiles + 2, 1);
         const int2 tile = tiles[ti];
         ProbDesc &P = desc[tile.x];
-        if (P.sc.done) continue;                     // uniform over the CTA
+        if (P.sc.done) {                             // uniform over the CTA
+            __syncthreads();                         // s_next[par] is visible to the CTA
+            continue;
+        }
         const double beta = P.sc.it == 0 ? 0.0 : P.sc.beta;
         const double xa = P.sc.x_alpha;
         const int64_t e0 = (int64_t)tile.y * P.te;
@@ -220,6 +233,13 @@ eng_ax_head(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const i
             }
         }
         __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();   // this CTA's counter increments come before its exit count
+        if (atomicAdd(ntiles + 3, 1) == (int)gridDim.x - 1) {
+            ntiles[2] = 0;
+            ntiles[3] = 0;
+        }
     }
 }
 
@@ -898,7 +918,7 @@ struct EngSlot {
 struct NGroup {
     int lpt = 0, te = 0;                 // tuned (0: not yet)
     int2 *d_ax = nullptr, *d_ds = nullptr;
-    int *d_cnt = nullptr;                // [0] = ax tiles, [1] = dssum tiles
+    int *d_cnt = nullptr;                // [0] = ax tiles, [1] = dssum tiles, [2] [3] the FP64 head's tile counter
     int cap_ax = 0, cap_ds = 0;
     std::vector<int> slots;
     bool dirty = false;
@@ -1229,9 +1249,9 @@ static nb_status ensure_group(nb_engine *g, NGroup &G, int n, int64_t max_tiles_
         nb_status s = host_gll(n, xi, w);
         if (s != NB_OK) return s;
         if ((s = host_dmat(n, xi, G.D)) != NB_OK) return s;
-        cudaError_t e = dev_alloc((void **)&G.d_cnt, 2 * sizeof(int));
+        cudaError_t e = dev_alloc((void **)&G.d_cnt, 4 * sizeof(int));
         if (e != cudaSuccess) return cuda_fail(e, "alloc tile counts");
-        NB_CUDA(cudaMemsetAsync(G.d_cnt, 0, 2 * sizeof(int), g->stream));
+        NB_CUDA(cudaMemsetAsync(G.d_cnt, 0, 4 * sizeof(int), g->stream));
     }
     auto grow = [&](int2 **arr, int *cap, int64_t need) -> nb_status {
         if (need <= *cap) return NB_OK;
