@@ -172,17 +172,10 @@ __device__ __forceinline__ u128 cg_head_pipelined(const AxDfArgs &a, double beta
             }
         }
     };
-    // the box-face bits (point_faces) of this thread's points in the final
-    // pass, six bits per point, five points per word, computed once
+    // the box-face bits of this thread's points in the final pass, computed once
     constexpr int PPT = df_points_per_thread<N, T>();
-    unsigned pfw[(PPT + 4) / 5];
-#pragma unroll
-    for (int k = 0; k < (PPT + 4) / 5; k++) pfw[k] = 0u;
-#pragma unroll
-    for (int k = 0; k < PPT; k++) {
-        const int q = t + k * T;
-        if (q < N3) pfw[k / 5] |= point_faces<N>(q) << (6 * (k % 5));
-    }
+    FaceBits<N, T, PPT> pf;
+    pf.init();
     u128 acc = 0;
     int64_t e = blockIdx.x;
     if (e < a.E) stage(e, S0);
@@ -254,7 +247,7 @@ __device__ __forceinline__ u128 cg_head_pipelined(const AxDfArgs &a, double beta
                 if (PPT * T != N3 && q >= N3) break;
                 const float2 s = dfa::add(dfa::add(X[q], S4[q]), S5[q]);
                 double wv = dfa::join_scaled(s, sh_out);
-                if ((pfw[kk / 5] >> (6 * (kk % 5))) & bf)
+                if (pf[kk] & bf)
                     wv = 0.0;
                 else
                     de = fma(wv, p[q], de);

@@ -82,7 +82,8 @@ struct ProbDesc {
 // order: the tile schedule is static, so the partial is deterministic.
 template <int N, int T>
 __device__ __forceinline__ double eng_head_tile(const ProbDesc &P, int64_t e0, int64_t e1, double beta,
-                                                double xa, const DfEo<N> &D, float2 *sm, const unsigned *pf) {
+                                                double xa, const DfEo<N> &D, float2 *sm,
+                                                const FaceBits<N, T, df_points_per_thread<N, T>()> &pf) {
     constexpr int N2 = N * N, N3 = N * N * N;
     const int t = threadIdx.x;
     const double pn = P.sc.it == 0 ? P.sc.rr : P.sc.pn2;
@@ -188,8 +189,8 @@ eng_ax_head(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, int *__
     extern __shared__ float2 sm[];
     __shared__ int s_last;
     __shared__ double red[32];
-    unsigned pf[df_points_per_thread<N, T>()];
-    df_point_masks<N, T>(pf);
+    FaceBits<N, T, df_points_per_thread<N, T>()> pf;
+    pf.init();
     // Tiles after the first come from a counter (ntiles[2]), so that SMs
     // that run slower take fewer; a tile's result does not depend on the CTA
     // that computes it.  Thread 0 takes the next index at the start of a

@@ -119,6 +119,26 @@ __device__ __forceinline__ unsigned point_faces(int q) {
            ((unsigned)(j == N - 1) << 3) | ((unsigned)(k == 0) << 4) | ((unsigned)(k == N - 1) << 5);
 }
 
+// The point_faces bits of the points q = threadIdx.x + k T (k < PPT) that a
+// thread owns in a pointwise pass, six bits per point, five points per
+// 32-bit word: one register per five points instead of one per point.
+// pf[k] with a compile-time k is a shift and a mask.
+template <int N, int T, int PPT>
+struct FaceBits {
+    static constexpr int W = (PPT + 4) / 5;
+    unsigned w[W];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int k = 0; k < W; k++) w[k] = 0u;
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+            const int q = (int)threadIdx.x + k * T;
+            if (q < N * N * N) w[k / 5] |= point_faces<N>(q) << (6 * (k % 5));
+        }
+    }
+    __device__ __forceinline__ unsigned operator[](int k) const { return (w[k / 5] >> (6 * (k % 5))) & 63u; }
+};
+
 // Faces of element (ex,ey,ez) shared with a neighbour, in point_faces' bit
 // order: log2 of a point's multiplicity is popc(point_faces & shared_faces).
 __device__ __forceinline__ unsigned shared_faces(int ex, int ey, int ez, const Mesh &m) {
