@@ -79,7 +79,7 @@ struct ProbDesc {
 // next element is staged while the current one's partials are summed: four
 // barriers per element.  Returns this thread's share of the tile's <w,p>_c
 // (local products at the points off the box faces), an FP64 sum in element
-// order: the tile schedule is static, so the partial is deterministic.
+// order, so the tile's partial does not depend on which CTA computed it.
 template <int N, int T>
 __device__ __forceinline__ double eng_head_tile(const ProbDesc &P, int64_t e0, int64_t e1, double beta,
                                                 double xa, const DfEo<N> &D, float2 *sm,
