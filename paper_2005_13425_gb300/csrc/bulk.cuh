@@ -50,6 +50,15 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
         : "memory");
 }
 
+// A hint to bring [p, p + bytes) into L2 (the 16-byte-aligned part of the
+// range): one bulk prefetch issued by one thread, with nothing to wait for.
+__device__ __forceinline__ void l2_prefetch(const void *p, unsigned long long bytes) {
+    const unsigned long long a = (unsigned long long)__cvta_generic_to_global(p);
+    const unsigned long long lo = (a + 15ull) & ~15ull, hi = (a + bytes) & ~15ull;
+    if (hi > lo)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
+}
+
 // An L2 policy that marks lines for early eviction (data read once).
 __device__ __forceinline__ uint64_t l2_evict_first_policy() {
     uint64_t pol;
