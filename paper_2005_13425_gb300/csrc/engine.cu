@@ -520,6 +520,12 @@ eng_m_head(ProbDesc *__restrict__ desc, const int2 *__restrict__ tiles, const in
             io.x = P.z32 + eb;
             io.w = P.w32 + eb;
             io.g = P.g32 + e * 6 * N3;
+            if (threadIdx.x == 0 && e + 1 < e1) {   // the next element into L2 (see eng_head_tile)
+                l2_prefetch(P.g32 + (e + 1) * 6 * N3, sizeof(float) * 6 * N3);
+                l2_prefetch(P.r32 + (e + 1) * N3, sizeof(float) * N3);
+                l2_prefetch(P.p32 + (e + 1) * N3, sizeof(float) * N3);
+                if (xa != 0.f) l2_prefetch(P.z32 + (e + 1) * N3, sizeof(float) * N3);
+            }
             int ex, ey, ez;
             element_coords(e, m, ex, ey, ez);
             f32_element<N, 1, T>(io, beta, xa, ex, ey, ez, m, D, smf, dot);
