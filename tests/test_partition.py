@@ -13,7 +13,8 @@ definition.  Checked against the unpartitioned oracle:
 * 30 fixed CG iterations follow the oracle's CG (rho history and x to 1e-8:
   only the order of the inner-product sums differs);
 * the same with two gloo ranks (world size 2, three slabs: rank 0 holds two
-  of them, so local copies and point-to-point exchanges both occur).
+  of them, so local copies and point-to-point exchanges both occur) and with
+  three (one slab per rank: the middle rank exchanges with both neighbours).
 """
 import json
 import multiprocessing as mp
@@ -194,18 +195,22 @@ def _gloo_worker(rank, world, port, outdir):
         dist.destroy_process_group()
 
 
-def test_partitioned_box_two_gloo_ranks(oracle, tmp_path):
+@pytest.mark.parametrize("world", [2, 3])
+def test_partitioned_box_gloo_ranks(oracle, tmp_path, world):
+    """world 2: rank 0 holds two of the three slabs (a local copy and a
+    point-to-point exchange); world 3: one slab per rank, so the middle rank
+    exchanges planes with both neighbours in both directions."""
     ctx = mp.get_context("spawn")
     port = _free_port()
-    ps = [ctx.Process(target=_gloo_worker, args=(r, 2, port, str(tmp_path))) for r in range(2)]
+    ps = [ctx.Process(target=_gloo_worker, args=(r, world, port, str(tmp_path))) for r in range(world)]
     for p in ps:
         p.start()
     for p in ps:
         p.join(timeout=300)
         assert p.exitcode == 0
-    parts = [np.load(tmp_path / f"rank{r}.npz") for r in range(2)]
-    meta = [json.load(open(tmp_path / f"rank{r}.json")) for r in range(2)]
-    assert meta[0]["hist"] == meta[1]["hist"]                  # the all-reduced scalars agree
+    parts = [np.load(tmp_path / f"rank{r}.npz") for r in range(world)]
+    meta = [json.load(open(tmp_path / f"rank{r}.json")) for r in range(world)]
+    assert all(m["hist"] == meta[0]["hist"] for m in meta)     # the all-reduced scalars agree
     w = np.concatenate([p["w"] for p in parts])
     x = np.concatenate([p["x"] for p in parts])
     check_against_oracle(oracle, w, x, meta[0]["it"], meta[0]["hist"], meta[0]["bad"])
